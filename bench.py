@@ -1,0 +1,369 @@
+"""Benchmark of the motion-focus path on GB300: 1080p frames/s and % of HBM roofline.
+
+Workload: one stream of 900 frames at 1920x1080 (fx = fy = 1500, principal
+point (960, 540)), window 16, 15-sample fit, ACCEL mode, FP32 depth and
+maps; synthetic walker with turns, depth ray-cast from a seeded box scene
+(ring of 8 rendered images over 900 distinct HBM planes).  One step is one
+pass of the whole path over the batch through the C ABI: reset, push of the
+900 poses and depth planes (anchoring + motion points), and mf_get_maps of
+all 900 frames (motion-focus map, guided depth, per-frame records).
+
+The timed region holds K steps between CUDA events on the library's stream,
+bracketed by a barrier and synchronisation; the inputs (7.5 GB) and outputs
+(15 GB) are far larger than L2, so no flush is needed.  ``e2e`` repeats the
+measurement with host buffers (pinned), host<->device copies inside.
+
+``--impl reference`` times the FP64 CPU oracle (the test oracle, not a
+product path) on the host cores on a bounded sample of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "1080p frames/s & % HBM roofline; p99 frame latency, served vs plain, same GPU"
+WIDTH, HEIGHT, FRAMES, WINDOW, SMOOTH = 1920, 1080, 900, 16, 15
+BYTES_PER_PX = 12  # depth read + focus map write + guided depth write (FP32)
+FRAME_BYTES = WIDTH * HEIGHT * BYTES_PER_PX
+PROFILE = os.path.join(ROOT, "profiles", "map_kernel_1080p_f32.txt")
+MAP_SRC = os.path.join(ROOT, "paper_2601_07154_gb300", "csrc", "mf_map_kernel.cu")
+
+
+def env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def workload_config(frames=FRAMES):
+    return {"workload": f"1 stream, {frames} frames 1920x1080, window 16, K=15 fit, ACCEL, "
+                        "FP32 depth+maps, walker with turns, ray-cast box scene",
+            "frames_per_step": frames, "width": WIDTH, "height": HEIGHT, "window": WINDOW,
+            "smooth_len": SMOOTH, "l2": "inputs+outputs 22.4 GB per step >> 129 MB L2 (no flush)"}
+
+
+# ------------------------------------------------------------------ peaks --
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def profiled_traffic(frames):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the source."""
+    try:
+        text = open(PROFILE).read()
+    except OSError:
+        return None
+    src_hash = hashlib.sha256(open(MAP_SRC, "rb").read()).hexdigest()[:16]
+    vals = {}
+    for line in text.splitlines():
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("source_sha256_16") != src_hash:
+        return None
+    try:
+        per_frame = float(vals["dram_bytes_per_frame"])
+    except (KeyError, ValueError):
+        return None
+    return per_frame * frames
+
+
+# ----------------------------------------------------------------- clocks --
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_id), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def smi_index(torch, dev, local):
+    """nvidia-smi index of the torch device: by UUID, else PCI bus, else the only GPU."""
+    try:
+        out = subprocess.run(["nvidia-smi", "--query-gpu=index,uuid,pci.bus_id",
+                              "--format=csv,noheader"], capture_output=True, text=True,
+                             timeout=20).stdout.strip().splitlines()
+    except (OSError, subprocess.SubprocessError):
+        return local
+    rows = [[c.strip() for c in ln.split(",")] for ln in out if ln.count(",") >= 2]
+    if len(rows) == 1:
+        return rows[0][0]
+    props = torch.cuda.get_device_properties(dev)
+    uuid = str(getattr(props, "uuid", ""))
+    for idx, u, bus in rows:
+        if uuid and uuid in u:
+            return idx
+        pci = getattr(props, "pci_bus_id", None)
+        if pci is not None and bus.lower().endswith(f"{int(pci):02x}:00.0"):
+            return idx
+    return local
+
+
+# ------------------------------------------------------------ GPU arm ----
+def make_inputs(torch, dev, frames):
+    from synth import hd_stream
+    w = hd_stream()
+    ring = torch.from_numpy(np.stack([w.depth(k) for k in range(w.ring)])).to(dev)
+    idx = torch.tensor([k % w.ring for k in range(frames)], device=dev)
+    depth = ring[idx].contiguous()
+    poses = torch.from_numpy(np.ascontiguousarray(w.poses[:frames])).to(dev)
+    return w, poses, depth
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2601_07154_gb300 as mf
+
+    world = env_int("WORLD_SIZE", 1)
+    rank = env_int("RANK", 0)
+    local = env_int("LOCAL_RANK", 0)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    frames = args.frames
+    w, poses, depth = make_inputs(torch, dev, frames)
+    K = w.K()
+    M = torch.empty((frames, HEIGHT, WIDTH), dtype=torch.float32, device=dev)
+    G = torch.empty_like(M)
+    info = torch.empty(frames * 64, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(dev)
+    s = mf.MotionFocusStream(WIDTH, HEIGHT, window=WINDOW, smooth_len=SMOOTH, device=dev,
+                             cuda_stream=stream, time_kernels=True)
+    h = s.handle
+    Kh = np.ascontiguousarray(K)
+
+    def step():
+        mf.mf_reset_stream(h)
+        mf.mf_push_frames(h, frames, poses, depth, Kh)
+        got = mf.mf_get_maps(h, frames, M, G, info, None)
+        assert got == frames
+
+    for _ in range(args.warmup):
+        step()
+    stream.synchronize()
+    s0 = s.stats()
+    l0 = mf.mf_total_kernel_launches()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(smi_index(torch, dev, local))
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    ev1.synchronize()
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    launches = mf.mf_total_kernel_launches() - l0
+    s1 = s.stats()
+    map_ms = (s1.map_kernel_ms - s0.map_kernel_ms) / max(1, s1.map_launches - s0.map_launches)
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = frames * args.steps * world / (ms / 1000.0)
+
+    e2e = None
+    if rank == 0 and not args.no_e2e:
+        del M, G
+        e2e = run_e2e(torch, mf, w, depth, dev, args)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(w, args.cpu_seconds)
+    s.close()
+    if rank == 0:
+        peak, kind = hbm_peak()
+        achieved = frames * FRAME_BYTES / (map_ms / 1000.0) / 1e9
+        rec = {
+            "metric": METRIC, "value": round(value, 2), "unit": "frames/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "pose_dtype": "f64", "data": "synthetic (seeded walker poses, ray-cast depth)",
+            "config": workload_config(frames),
+            "mpx_per_s": round(value * WIDTH * HEIGHT / 1e6, 1),
+            "step_hbm_gbs": round(value / world * FRAME_BYTES / 1e9, 1),
+            "roofline": {"bound": "hbm", "kernel": "map_kernel", "achieved": round(achieved, 1),
+                         "peak": peak, "peak_kind": kind, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": profiled_traffic(frames),
+                         "algorithmic_bytes_per_launch": frames * FRAME_BYTES,
+                         "launch_ms": round(map_ms, 4)},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+        }
+        print(json.dumps(rec), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_e2e(torch, mf, w, depth_dev, dev, args):
+    """Same metric through the C ABI with pinned host inputs and outputs."""
+    FR = int(depth_dev.shape[0])
+    depth_h = torch.empty((FR, HEIGHT, WIDTH), dtype=torch.float32, pin_memory=True)
+    depth_h.copy_(depth_dev)
+    M_h = torch.empty_like(depth_h, pin_memory=True)
+    G_h = torch.empty_like(depth_h, pin_memory=True)
+    info_h = np.empty(FR, dtype=mf._mf.FRAME_INFO_DTYPE)
+    poses_h = np.ascontiguousarray(w.poses[:FR])
+    Kh = np.ascontiguousarray(w.K())
+    s = mf.MotionFocusStream(WIDTH, HEIGHT, window=WINDOW, smooth_len=SMOOTH, device=dev)
+    h = s.handle
+
+    def step():
+        mf.mf_reset_stream(h)
+        mf.mf_push_frames(h, FR, poses_h, depth_h, Kh)
+        assert mf.mf_get_maps(h, FR, M_h, G_h, info_h, None) == FR
+
+    for _ in range(2):
+        step()
+    n = max(3, args.e2e_steps)
+    t0 = time.perf_counter()
+    for _ in range(n):
+        step()
+    dt = time.perf_counter() - t0
+    s.close()
+    return {"value": round(FR * n / dt, 2), "unit": "frames/s", "steps": n,
+            "h2d_bytes_per_step": FR * 96 + FR * WIDTH * HEIGHT * 4,
+            "d2h_bytes_per_step": 2 * FR * WIDTH * HEIGHT * 4 + FR * 64}
+
+
+# ------------------------------------------------------------- CPU oracle --
+def oracle_sample(w, frames, rows):
+    """Oracle frames/s on frames (full pose path) x rows of their maps."""
+    import oracle as O
+    p = O.Params(WIDTH, HEIGHT, window=WINDOW, smooth_len=SMOOTH)
+    ref = O.OracleStream(p)
+    ref.push(w.poses, None, w.K())
+    ys_all = np.arange(HEIGHT)
+    t0 = time.perf_counter()
+    for n in frames:
+        pts = ref.points(n)
+        ys = ys_all[rows]
+        yy = np.repeat(ys, WIDTH)
+        xx = np.tile(np.arange(WIDTH), len(ys))
+        M = O.focus_map(pts, WIDTH, HEIGHT, xx, yy)
+        D = w.depth(n)[ys, :].reshape(-1)
+        O.guided_depth(M, D, 1.0)
+    dt = time.perf_counter() - t0
+    credited = len(frames) * (len(range(HEIGHT)[rows]) / HEIGHT)
+    return credited / dt, dt
+
+
+def cpu_baseline(w, seconds):
+    # calibrate on a 64-row band, then size the sample to ~`seconds`
+    rate, dt = oracle_sample(w, [450], slice(0, 64))
+    nframes = max(1, min(16, int(seconds * rate)))
+    frames = list(range(450, 450 + nframes))
+    rate, dt = oracle_sample(w, frames, slice(0, HEIGHT))
+    return {"value": round(rate, 4), "unit": "frames/s", "cores": 1, "kind": "oracle",
+            "sample": f"{nframes} full 1920x1080 frames ({frames[0]}..{frames[-1]}) of the "
+                      f"900-frame workload, FP64 numpy oracle, {dt:.1f} s"}
+
+
+def run_reference(args):
+    world = env_int("WORLD_SIZE", 1)
+    rank = env_int("RANK", 0)
+    if rank != 0:
+        return
+    from synth import hd_stream
+    w = hd_stream()
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    rate0, _ = oracle_sample(w, [450], slice(0, 16))
+    rows = int(max(1, min(HEIGHT, budget * rate0 * HEIGHT)))
+    for k in range(args.warmup):
+        oracle_sample(w, [450 + k % 400], slice(0, rows))
+    t0 = time.perf_counter()
+    credited = 0.0
+    for k in range(args.steps):
+        _, _ = oracle_sample(w, [450 + k % 400], slice(0, rows))
+        credited += rows / HEIGHT
+    dt = time.perf_counter() - t0
+    value = credited / dt
+    rec = {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "frames/s",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(1000 * dt / args.steps, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": workload_config(),
+           "cpu_baseline": {"value": round(value, 5), "unit": "frames/s", "cores": 1,
+                            "kind": "oracle",
+                            "sample": f"per step: one frame's motion points + {rows} of 1080 "
+                                      "map rows (credited as that fraction of a frame)"},
+           "e2e": {"value": round(value, 5), "unit": "frames/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(rec), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--frames", type=int, default=FRAMES,
+                    help="frames per step (default: the full 900-frame workload; "
+                         "smaller values only for profiling captures)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,259 @@
+/*
+ * mf.h -- C ABI of libmf, the GB300 (sm_103a) motion-focus library.
+ *
+ * The library implements the data-parallel path of "Motion Focus Recognition
+ * in Fast-Moving Egocentric Video" (arXiv 2601.07154, Section 2.3): from a
+ * stream of camera poses T_t^{w->c}, per-pixel depth maps D_t and pinhole
+ * intrinsics K it produces, for every frame, the motion-focus map M of Eq. 7
+ * and the motion-guided depth map of Fig. 1(iii) / Fig. 5.
+ *
+ * Conventions used by every entry point
+ *   - Poses are world-to-camera rigid transforms stored as 3x4 row-major FP64
+ *     matrices [R | t] (12 doubles, 96 bytes per frame); the implied bottom
+ *     row is [0 0 0 1].  Camera axes: x right, y down, z forward (optical
+ *     axis); the world y axis is gravity ("down").
+ *   - Images (depth in, maps out) are height x width, row-major, one plane
+ *     per frame, planes contiguous (frame stride = width*height elements).
+ *     Pixel (x, y) -- column x, row y -- has its centre at image coordinates
+ *     (x, y).  Depth is camera z-depth in metres; 0 or a non-finite value
+ *     means "no depth".
+ *   - Pointers may be host memory (pageable or pinned) or device memory of
+ *     the stream's device; the library tells them apart with
+ *     cudaPointerGetAttributes.  Managed memory counts as device memory.
+ *   - Every entry point returns an mf_status (0 = MF_OK).  No exception or
+ *     signal crosses the ABI.  Calls on one mf_stream are not reentrant;
+ *     different mf_stream handles may be used from different threads.
+ */
+#ifndef MF_H
+#define MF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MF_VERSION 1
+#define MF_MAX_WINDOW 32       /* N motion points per frame */
+#define MF_MAX_HISTORY 64      /* window + smooth_len - 1 poses per frame */
+#define MF_MAX_DIM 16384       /* largest width / height */
+
+typedef struct mf_stream mf_stream; /* opaque, owned by the library */
+
+typedef enum { MF_F32 = 0, MF_BF16 = 1, MF_F16 = 2 } mf_dtype;
+
+/* Direction that is projected (Section 2.3):
+ *   ACCEL   -- acceleration (Eqs. 2-3), the paper's motion focus;
+ *   HEADING -- velocity, the "velocity-based projection" the paper contrasts
+ *              with after Eq. 6. */
+typedef enum { MF_MODE_ACCEL = 0, MF_MODE_HEADING = 1 } mf_mode;
+
+/* Coordinate frame of pushed poses (Section 2.2):
+ *   WORLD       -- poses already share one world frame;
+ *   BATCH_LOCAL -- every push is one inference batch in its own local frame;
+ *                  its first `overlap` frames repeat the previous batch's
+ *                  last frames and are used for incremental anchoring. */
+typedef enum { MF_POSES_WORLD = 0, MF_POSES_BATCH_LOCAL = 1 } mf_pose_frame;
+
+typedef enum {
+  MF_OK = 0,
+  MF_ERR_INVALID_ARG = 1,  /* bad descriptor, size, pointer or call order */
+  MF_ERR_INVALID_POSE = 2, /* reserved: poses are checked per frame, see MF_FRAME_BAD_POSE */
+  MF_ERR_OOM = 3,          /* a device or pinned allocation failed */
+  MF_ERR_NOT_READY = 4,    /* too many frames pending: call mf_get_maps first */
+  MF_ERR_TIMEOUT = 5,      /* a bounded wait expired (see mf_get_maps / mf_sync) */
+  MF_ERR_CUDA = 6,         /* a CUDA runtime call failed */
+  MF_ERR_ADMISSION = 7,    /* a server could not admit a stream (budget) */
+  MF_ERR_NO_DEVICE = 8     /* no usable CUDA device */
+} mf_status;
+
+/* Per-frame status reported in mf_frame_info.status. */
+typedef enum {
+  MF_FRAME_OK = 0,        /* at least one valid motion point */
+  MF_FRAME_EMPTY = 1,     /* no valid motion point: M = G = 0 */
+  MF_FRAME_BAD_POSE = 2   /* the frame's own pose is not a rigid transform */
+} mf_frame_status;
+
+/* mf_stream_desc.flags */
+#define MF_FLAG_TIME_KERNELS 1u /* time each map-kernel launch with CUDA events */
+
+/*
+ * Stream descriptor.  Fill with mf_stream_desc_init() and override fields.
+ *   width, height        map resolution == depth resolution (1..MF_MAX_DIM)
+ *   calib_width/height   resolution the intrinsics K refer to; 0 = same as
+ *                        the map.  K is rescaled to the map resolution
+ *                        ("real camera intrinsics as physical constraints",
+ *                        Section 1; K of Eq. 5).
+ *   window               W = N motion points per frame (Eq. 7), 1..32
+ *   smooth_len           K samples of the causal least-squares fit that
+ *                        generalises Eqs. 2-3 (3 reproduces Eq. 3 exactly);
+ *                        >= 3 for ACCEL, >= 2 for HEADING;
+ *                        window + smooth_len - 1 <= MF_MAX_HISTORY
+ *   mode                 mf_mode
+ *   pose_frame, overlap  mf_pose_frame and the shared frame count O of
+ *                        Section 2.2 (BATCH_LOCAL: O >= 1; WORLD: O == 0)
+ *   depth_dtype          storage type of pushed depth (mf_dtype)
+ *   map_dtype            storage type of both output maps (mf_dtype)
+ *   max_pending          frames that may wait between push and get_maps
+ *   sigma_rel            sigma of Eq. 7 as a fraction of fx (default 0.1)
+ *   s_lo, s_hi           clamp of the motion magnitude s_i (0.25, 4)
+ *   depth_ref_m          d0 of the guided depth G = M min(1, d0/D) (1.0 m)
+ *   cuda_stream          cudaStream_t to run on, including the runtime's
+ *                        cudaStreamLegacy (0x1) and cudaStreamPerThread
+ *                        (0x2) handles; NULL = a library-owned non-blocking
+ *                        stream (not ordered with the legacy default stream)
+ *   dev_alloc/dev_free   optional device allocator (e.g. PyTorch's caching
+ *                        allocator); NULL = cudaMalloc / cudaFree
+ */
+typedef struct {
+  int32_t width, height;
+  int32_t calib_width, calib_height;
+  int32_t window;
+  int32_t smooth_len;
+  int32_t mode;
+  int32_t pose_frame;
+  int32_t overlap;
+  int32_t depth_dtype;
+  int32_t map_dtype;
+  int32_t max_pending;
+  uint32_t flags;
+  int32_t reserved0;
+  double sigma_rel, s_lo, s_hi, depth_ref_m;
+  void* cuda_stream;
+  void* (*dev_alloc)(size_t bytes, void* ctx);
+  void (*dev_free)(void* ptr, void* ctx);
+  void* alloc_ctx;
+} mf_stream_desc;
+
+/* Per-frame results (64 bytes). */
+typedef struct {
+  int64_t frame_index;   /* emitted-frame index within the stream, from 0 */
+  int32_t status;        /* mf_frame_status */
+  int32_t n_valid;       /* valid motion points = Z of Eq. 7 */
+  uint32_t valid_mask;   /* bit s: slot s (frame n-W+1+s) is valid */
+  int32_t focus_valid;   /* the newest point (slot W-1) is valid */
+  double focus_u, focus_v;     /* Eq. 6 of the newest point, pixels; 0 if invalid */
+  int32_t focus_px_x, focus_px_y; /* rint(focus) if inside the frame, else -1 */
+  int32_t argmax_x, argmax_y;  /* largest M (ties: lowest y*width+x); -1 if empty */
+  float map_max;               /* M at the argmax (FP32 arithmetic value) */
+  int32_t reserved;
+} mf_frame_info;
+
+/* One motion point (slot s of a frame), FP64 (40 bytes). */
+typedef struct {
+  double u, v;      /* Eq. 6 projection at the map resolution */
+  double sigma;     /* sigma * s_i of Eq. 7, pixels */
+  double s;         /* motion magnitude s_i (clamped ratio to the mean) */
+  int32_t valid;
+  int32_t reserved;
+} mf_motion_point;
+
+typedef struct {
+  int64_t frames_pushed;     /* poses received, overlap included */
+  int64_t frames_emitted;    /* non-overlapping frames (Section 2.2) */
+  int64_t frames_rendered;   /* frames whose maps were produced */
+  int64_t kernel_launches;   /* this stream's kernel launches */
+  int64_t map_launches;      /* map-kernel launches timed (MF_FLAG_TIME_KERNELS) */
+  double map_kernel_ms;      /* summed CUDA-event time of those launches */
+  int64_t device_bytes;      /* device memory the stream holds */
+} mf_stats;
+
+/* Fill *d with defaults (sigma_rel 0.1, s in [0.25, 4], d0 = 1 m, ACCEL,
+ * WORLD poses, FP32 depth and maps, window 8, smooth_len 15,
+ * max_pending 1024).  width/height stay 0 and must be set. */
+void mf_stream_desc_init(mf_stream_desc* d);
+
+/*
+ * Open a stream: validates *d, allocates the pose history and the pending
+ * frame records on the current CUDA device, and precomputes the
+ * least-squares weights (Eqs. 2-3 generalised).  No kernel runs.
+ * Returns MF_ERR_INVALID_ARG for an invalid descriptor, MF_ERR_OOM, or
+ * MF_ERR_NO_DEVICE.  *out receives the handle (NULL on error).
+ */
+int mf_open_stream(const mf_stream_desc* d, mf_stream** out);
+
+/*
+ * Push one batch of n frames (Section 2.2; Eqs. 1-6 per frame).
+ *   poses_w2c_3x4  n x 12 FP64 world-to-camera poses, host or device.
+ *   depth          n depth planes of depth_dtype (height x width each),
+ *                  host or device.  In BATCH_LOCAL mode after the first
+ *                  push, planes 0..overlap-1 belong to overlap frames and
+ *                  are not read (they may hold anything).  May be NULL:
+ *                  then the guided-depth output of these frames is 0.
+ *   K              host pointer to 4 FP64 values fx, fy, cx, cy at the
+ *                  calibration resolution, in force for this batch.
+ * Emits frames overlap..n-1 (all n on the first push or in WORLD mode):
+ * anchors them (BATCH_LOCAL, gravity-locked yaw + translation), appends
+ * them to the pose history and computes their motion points on the GPU.
+ * Host inputs are copied before the call returns; device inputs are read
+ * asynchronously on the stream, pose buffers before any later push and
+ * depth buffers when the frames are rendered by mf_get_maps -- keep them
+ * unchanged until then.  A pose whose rotation is not orthonormal to 1e-6
+ * (or not finite) makes its frame MF_FRAME_BAD_POSE and invalidates every
+ * motion point whose fit uses it; a bad anchor makes the whole batch bad.
+ * Errors: MF_ERR_INVALID_ARG (n < 1, n <= overlap on a later BATCH_LOCAL
+ * push, NULL poses/K), MF_ERR_NOT_READY (more than max_pending frames would
+ * wait), MF_ERR_OOM, MF_ERR_CUDA.  On error nothing is ingested.
+ */
+int mf_push_frames(mf_stream* s, int32_t n, const double* poses_w2c_3x4,
+                   const void* depth, const double* K);
+
+/*
+ * Render up to max_frames pending frames, oldest first, into the caller's
+ * buffers (Eq. 7 and the motion-guided depth), and report them.
+ *   focus_map      n_out planes of map_dtype (height x width), or NULL
+ *   guided_depth   n_out planes of map_dtype, or NULL
+ *   info           n_out mf_frame_info records, or NULL
+ *   points         n_out * window mf_motion_point records (slot-major per
+ *                  frame), or NULL
+ *   n_out          receives the number of frames returned (0 if none pend)
+ *   timeout_ns     bound on the wait used when an output is host memory;
+ *                  < 0 waits without bound.
+ * If every non-NULL output is device memory the call only enqueues work on
+ * the stream and returns; the results are ready once the stream reaches
+ * that point (mf_sync).  If any output is host memory the call waits for
+ * the copies; on MF_ERR_TIMEOUT the frames count as returned but copies into
+ * the caller's host buffers may still be in flight: keep those buffers
+ * alive until mf_sync or mf_close_stream returns.
+ */
+int mf_get_maps(mf_stream* s, int32_t max_frames, void* focus_map, void* guided_depth,
+                mf_frame_info* info, mf_motion_point* points, int32_t* n_out,
+                int64_t timeout_ns);
+
+/* Wait (bounded by timeout_ns; < 0 = no bound) until all work enqueued on
+ * the stream has finished.  MF_ERR_TIMEOUT if the bound expires. */
+int mf_sync(mf_stream* s, int64_t timeout_ns);
+
+/* Number of emitted frames not yet returned by mf_get_maps. */
+int mf_pending_frames(const mf_stream* s, int32_t* n);
+
+/* Forget the pose history and pending frames (frame indices restart at 0);
+ * keeps the allocations.  Does not wait: work already enqueued finishes in
+ * stream order, and pending frames that were never returned are dropped. */
+int mf_reset_stream(mf_stream* s);
+
+/* Counters and, with MF_FLAG_TIME_KERNELS, map-kernel timings (waits for
+ * the timed launches to finish). */
+int mf_stream_stats(mf_stream* s, mf_stats* out);
+
+/* Wait for the stream's work, free everything the stream holds. */
+int mf_close_stream(mf_stream* s);
+
+/* Static description of a status code. */
+const char* mf_status_string(int status);
+
+/* MF_VERSION of the loaded library. */
+int mf_version(void);
+
+/* Kernel launches made by this process through the library (all streams). */
+int64_t mf_total_kernel_launches(void);
+
+/* Text of the last error raised on the calling thread ("" if none); valid
+ * until the thread's next failing call. */
+const char* mf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MF_H */

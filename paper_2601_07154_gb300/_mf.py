@@ -1,0 +1,198 @@
+"""ctypes binding of libmf's C ABI (include/mf.h): argument marshalling only.
+
+Every function here has the name of the C entry point it wraps and only
+converts arguments (torch tensors, numpy arrays or raw integer addresses to
+pointers; Python numbers to C scalars) and raises ``MFError`` on a non-zero
+status.  All computation happens in the library's CUDA kernels.  Loading
+fails loudly when libmf.so has not been built: there is no fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmf.so")
+
+MF_F32, MF_BF16, MF_F16 = 0, 1, 2
+MF_MODE_ACCEL, MF_MODE_HEADING = 0, 1
+MF_POSES_WORLD, MF_POSES_BATCH_LOCAL = 0, 1
+MF_FRAME_OK, MF_FRAME_EMPTY, MF_FRAME_BAD_POSE = 0, 1, 2
+MF_FLAG_TIME_KERNELS = 1
+(MF_OK, MF_ERR_INVALID_ARG, MF_ERR_INVALID_POSE, MF_ERR_OOM, MF_ERR_NOT_READY,
+ MF_ERR_TIMEOUT, MF_ERR_CUDA, MF_ERR_ADMISSION, MF_ERR_NO_DEVICE) = range(9)
+
+EXPORTED = ("mf_stream_desc_init", "mf_open_stream", "mf_push_frames", "mf_get_maps",
+            "mf_sync", "mf_pending_frames", "mf_reset_stream", "mf_stream_stats",
+            "mf_close_stream", "mf_status_string", "mf_version", "mf_total_kernel_launches",
+            "mf_last_error")
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class MFStreamDesc(ctypes.Structure):
+    _fields_ = [
+        ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+        ("calib_width", ctypes.c_int32), ("calib_height", ctypes.c_int32),
+        ("window", ctypes.c_int32), ("smooth_len", ctypes.c_int32),
+        ("mode", ctypes.c_int32), ("pose_frame", ctypes.c_int32),
+        ("overlap", ctypes.c_int32), ("depth_dtype", ctypes.c_int32),
+        ("map_dtype", ctypes.c_int32), ("max_pending", ctypes.c_int32),
+        ("flags", ctypes.c_uint32), ("reserved0", ctypes.c_int32),
+        ("sigma_rel", ctypes.c_double), ("s_lo", ctypes.c_double),
+        ("s_hi", ctypes.c_double), ("depth_ref_m", ctypes.c_double),
+        ("cuda_stream", ctypes.c_void_p),
+        ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_ctx", ctypes.c_void_p),
+    ]
+
+
+class MFStats(ctypes.Structure):
+    _fields_ = [
+        ("frames_pushed", ctypes.c_int64), ("frames_emitted", ctypes.c_int64),
+        ("frames_rendered", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+        ("map_launches", ctypes.c_int64), ("map_kernel_ms", ctypes.c_double),
+        ("device_bytes", ctypes.c_int64),
+    ]
+
+
+# numpy views of the C result records (layouts of include/mf.h)
+FRAME_INFO_DTYPE = np.dtype([
+    ("frame_index", "<i8"), ("status", "<i4"), ("n_valid", "<i4"), ("valid_mask", "<u4"),
+    ("focus_valid", "<i4"), ("focus_u", "<f8"), ("focus_v", "<f8"), ("focus_px_x", "<i4"),
+    ("focus_px_y", "<i4"), ("argmax_x", "<i4"), ("argmax_y", "<i4"), ("map_max", "<f4"),
+    ("reserved", "<i4")])
+MOTION_POINT_DTYPE = np.dtype([("u", "<f8"), ("v", "<f8"), ("sigma", "<f8"), ("s", "<f8"),
+                               ("valid", "<i4"), ("reserved", "<i4")])
+assert FRAME_INFO_DTYPE.itemsize == 64 and MOTION_POINT_DTYPE.itemsize == 40
+
+
+class MFError(RuntimeError):
+    def __init__(self, status, where, detail=""):
+        self.status = status
+        msg = f"{where}: {status_name(status)}"
+        if detail:
+            msg += f" ({detail})"
+        super().__init__(msg)
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"{LIB_PATH} is missing: build it with "
+            "`python -c 'import __graft_entry__ as g; g.build()'` (there is no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    lib.mf_stream_desc_init.argtypes = [ctypes.POINTER(MFStreamDesc)]
+    lib.mf_stream_desc_init.restype = None
+    lib.mf_open_stream.argtypes = [ctypes.POINTER(MFStreamDesc), ctypes.POINTER(vp)]
+    lib.mf_push_frames.argtypes = [vp, i32, vp, vp, vp]
+    lib.mf_get_maps.argtypes = [vp, i32, vp, vp, vp, vp, ctypes.POINTER(i32), i64]
+    lib.mf_sync.argtypes = [vp, i64]
+    lib.mf_pending_frames.argtypes = [vp, ctypes.POINTER(i32)]
+    lib.mf_reset_stream.argtypes = [vp]
+    lib.mf_stream_stats.argtypes = [vp, ctypes.POINTER(MFStats)]
+    lib.mf_close_stream.argtypes = [vp]
+    lib.mf_status_string.argtypes = [ctypes.c_int]
+    lib.mf_status_string.restype = ctypes.c_char_p
+    lib.mf_version.restype = ctypes.c_int
+    lib.mf_total_kernel_launches.restype = i64
+    lib.mf_last_error.restype = ctypes.c_char_p
+    for name in ("mf_open_stream", "mf_push_frames", "mf_get_maps", "mf_sync",
+                 "mf_pending_frames", "mf_reset_stream", "mf_stream_stats", "mf_close_stream"):
+        getattr(lib, name).restype = ctypes.c_int
+    return lib
+
+
+lib = _load()
+
+
+def status_name(status):
+    return lib.mf_status_string(int(status)).decode()
+
+
+def _check(rc, where):
+    if rc != MF_OK:
+        raise MFError(rc, where, lib.mf_last_error().decode(errors="replace"))
+
+
+def ptr(x):
+    """Address of a torch tensor, numpy array, ctypes object or int (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return ctypes.addressof(x)
+
+
+# ----------------------------------------------------------- entry points --
+def mf_stream_desc_init(**fields):
+    d = MFStreamDesc()
+    lib.mf_stream_desc_init(ctypes.byref(d))
+    for k, v in fields.items():
+        if not hasattr(d, k):
+            raise TypeError(f"unknown descriptor field {k}")
+        setattr(d, k, v)
+    return d
+
+
+def mf_open_stream(desc):
+    h = ctypes.c_void_p()
+    _check(lib.mf_open_stream(ctypes.byref(desc), ctypes.byref(h)), "mf_open_stream")
+    return h.value
+
+
+def mf_push_frames(s, n, poses, depth, K):
+    _check(lib.mf_push_frames(s, int(n), ptr(poses), ptr(depth), ptr(K)), "mf_push_frames")
+
+
+def mf_get_maps(s, max_frames, focus_map=None, guided_depth=None, info=None, points=None,
+                timeout_ns=-1):
+    n = ctypes.c_int32()
+    _check(lib.mf_get_maps(s, int(max_frames), ptr(focus_map), ptr(guided_depth), ptr(info),
+                           ptr(points), ctypes.byref(n), int(timeout_ns)), "mf_get_maps")
+    return n.value
+
+
+def mf_sync(s, timeout_ns=-1):
+    _check(lib.mf_sync(s, int(timeout_ns)), "mf_sync")
+
+
+def mf_pending_frames(s):
+    n = ctypes.c_int32()
+    _check(lib.mf_pending_frames(s, ctypes.byref(n)), "mf_pending_frames")
+    return n.value
+
+
+def mf_reset_stream(s):
+    _check(lib.mf_reset_stream(s), "mf_reset_stream")
+
+
+def mf_stream_stats(s):
+    st = MFStats()
+    _check(lib.mf_stream_stats(s, ctypes.byref(st)), "mf_stream_stats")
+    return st
+
+
+def mf_close_stream(s):
+    _check(lib.mf_close_stream(s), "mf_close_stream")
+
+
+def mf_status_string(status):
+    return status_name(status)
+
+
+def mf_version():
+    return lib.mf_version()
+
+
+def mf_total_kernel_launches():
+    return lib.mf_total_kernel_launches()
+
+
+def mf_last_error():
+    return lib.mf_last_error().decode(errors="replace")

@@ -1,0 +1,110 @@
+// Internal interfaces between the host engine (mf_stream.cpp) and the CUDA
+// kernels (mf_kernels.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/mf.h"
+
+namespace mf {
+
+constexpr int kMaxPts = MF_MAX_WINDOW;   // N motion points per frame
+constexpr int kMaxHist = MF_MAX_HISTORY; // W + K - 1 poses per frame
+constexpr int kTileW = 128;              // map-kernel tile width (32 lanes x 4 px)
+constexpr int kMapThreads = 256;         // 8 warps per map CTA
+
+// Thresholds of the motion-point validity test (Section 2.3, Eq. 6 readings).
+constexpr double kRigidTol = 1e-6;
+constexpr double kStaticRel = 1e-12;
+constexpr double kValidRelNorm = 1e-9;
+constexpr double kValidRelZ = 1e-3;
+
+// One emitted frame's motion points and per-frame results.  Written by the
+// window-points kernel, read by the map and finalize kernels.  The first
+// block holds the map kernel's operands for the valid points, compacted in
+// slot order: u = ux_hi + ux_lo and v = vy_hi + vy_lo split so that the
+// integer pixel coordinate minus the high part is exact in FP32, and the
+// Gaussian's 1 / (2 sigma^2) as a float pair c_hi + c_lo.
+struct alignas(16) FrameRec {
+  float ux_hi[kMaxPts], ux_lo[kMaxPts];
+  float vy_hi[kMaxPts], vy_lo[kMaxPts];
+  float c_hi[kMaxPts], c_lo[kMaxPts];
+  int32_t n_valid;
+  float inv_n;                 // 1 / Z of Eq. 7
+  uint32_t valid_mask;
+  int32_t status;
+  int64_t frame_index;
+  unsigned long long argmax_key;  // (bits of M << 32) | ~(y*W+x), max-reduced
+  double focus_u, focus_v;
+  int32_t focus_valid, focus_px_x, focus_px_y, pad0;
+  // slot-ordered FP64 records (slot s <-> frame n - W + 1 + s)
+  double u[kMaxPts], v[kMaxPts], sigma[kMaxPts], s[kMaxPts];
+  int32_t valid[kMaxPts];
+};
+
+struct IngestParams {
+  const double* in;        // n x 12 pushed poses (device)
+  int n;                   // frames in the push
+  int first;               // first emitted push frame (= overlap or 0)
+  int anchor;              // 1: gravity-locked anchoring against the history
+  double* ring;            // world-pose history, ring_mask+1 slots x 12
+  int32_t* ring_bad;
+  int64_t ring_mask;
+  int64_t e0;              // global index of the first emitted frame
+};
+
+struct PointsParams {
+  const double* ring;
+  const int32_t* ring_bad;
+  int64_t ring_mask;
+  FrameRec* recs;
+  int64_t rec_mask;
+  int64_t e0;              // global index of the first frame to process
+  int n_frames;
+  int window, smooth_len;
+  int width, height, calib_width, calib_height;
+  double K[4];             // fx, fy, cx, cy at the calibration resolution
+  double sigma_rel, s_lo, s_hi;
+  double w[kMaxHist];      // least-squares weights, w[k] multiplies q_{i-k}
+};
+
+struct MapParams {
+  const FrameRec* recs;
+  int64_t rec_mask;
+  int64_t f0;              // global index of the first frame of the launch
+  int n_frames;
+  int width, height;
+  int tiles_x, tiles_y, tile_h;
+  const void* depth;       // plane of frame f0, frames contiguous; may be NULL
+  void* M;                 // plane of frame f0 (may be NULL)
+  void* G;                 // (may be NULL)
+  float d0;
+};
+
+struct FinalizeParams {
+  const FrameRec* recs;
+  int64_t rec_mask;
+  int64_t f0;
+  int n_frames;
+  int width, window;
+  mf_frame_info* info;     // may be NULL
+  mf_motion_point* points; // may be NULL
+};
+
+// Launchers (return the CUDA launch status).  `launches` is incremented by
+// the number of kernels launched.
+cudaError_t launch_ingest(const IngestParams& p, cudaStream_t st, int64_t* launches);
+cudaError_t launch_points(const PointsParams& p, cudaStream_t st, int64_t* launches);
+cudaError_t launch_map(const MapParams& p, int window, int in_dtype, int out_dtype,
+                       cudaStream_t st, int64_t* launches);
+cudaError_t launch_finalize(const FinalizeParams& p, cudaStream_t st, int64_t* launches);
+cudaError_t launch_ring_copy(const double* src, const int32_t* src_bad, int64_t src_mask,
+                             double* dst, int32_t* dst_bad, int64_t dst_mask, int64_t first,
+                             int count, cudaStream_t st, int64_t* launches);
+
+// Map-kernel tile height used by the plain path.
+int map_tile_h(int width, int height, int window);
+
+}  // namespace mf

@@ -1,0 +1,761 @@
+// Host engine behind the C ABI of include/mf.h: stream state, staging of
+// host inputs and outputs, frame accounting of the sliding-batch ingestion
+// (Section 2.2), and the launches of the pose and map kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <new>
+#include <string>
+#include <thread>
+#include <utility>
+#include <vector>
+
+#include "mf_internal.h"
+
+using mf::FrameRec;
+
+namespace {
+
+std::atomic<int64_t> g_launches{0};
+thread_local std::string g_last_error;
+
+int fail(int status, const char* what, cudaError_t e = cudaSuccess) {
+  g_last_error = what;
+  if (e != cudaSuccess) {
+    g_last_error += ": ";
+    g_last_error += cudaGetErrorString(e);
+  }
+  return status;
+}
+
+#define MF_CUDA(call, what)                                       \
+  do {                                                            \
+    cudaError_t e_ = (call);                                      \
+    if (e_ != cudaSuccess) return fail(MF_ERR_CUDA, what, e_);    \
+  } while (0)
+
+size_t dtype_size(int dt) { return dt == MF_F32 ? 4 : 2; }
+
+int64_t pow2_at_least(int64_t v) {
+  int64_t c = 1;
+  while (c < v) c <<= 1;
+  return c;
+}
+
+// Device that was current on entry, restored on exit.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Exact least-squares derivative weights (Eqs. 2-3 generalised): the K
+// newest samples sit at tau_k = -k; the fit p(tau) = c0 + c1 tau + c2 tau^2
+// (a line when K = 2) gives d = 2 c2 (ACCEL) or c1 (HEADING) as
+// sum_k w_k q_{i-k}.  Solved by Cramer's rule in 128-bit integers, so each
+// weight is a reduced fraction and its double is correctly rounded.
+using i128 = __int128;
+
+i128 iabs128(i128 v) { return v < 0 ? -v : v; }
+i128 gcd128(i128 a, i128 b) {
+  a = iabs128(a);
+  b = iabs128(b);
+  while (b) {
+    i128 t = a % b;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+
+bool ls_weights(int K, int mode, double* w) {
+  const int deg = K >= 3 ? 2 : 1;
+  if (mode == MF_MODE_ACCEL && K < 3) return false;
+  if (K < 2) return false;
+  const int m = deg + 1;
+  i128 S[5] = {0, 0, 0, 0, 0};  // S[e] = sum_k tau_k^e
+  for (int k = 0; k < K; ++k) {
+    i128 t = -k, pw = 1;
+    for (int e = 0; e < 5; ++e) {
+      S[e] += pw;
+      pw *= t;
+    }
+  }
+  i128 N[3][3];
+  for (int a = 0; a < m; ++a)
+    for (int b = 0; b < m; ++b) N[a][b] = S[a + b];
+  // adjugate row of the wanted coefficient, and the determinant
+  const int want = mode == MF_MODE_ACCEL ? 2 : 1;
+  const i128 factor = mode == MF_MODE_ACCEL ? 2 : 1;
+  i128 adj[3] = {0, 0, 0}, det;
+  if (m == 2) {
+    det = N[0][0] * N[1][1] - N[0][1] * N[1][0];
+    // inverse row `want`=1 of a 2x2: [-N10, N00] / det
+    adj[0] = -N[1][0];
+    adj[1] = N[0][0];
+  } else {
+    auto minor = [&](int r, int c) {
+      int r0 = r == 0 ? 1 : 0, r1 = r == 2 ? 1 : 2;
+      int c0 = c == 0 ? 1 : 0, c1 = c == 2 ? 1 : 2;
+      return N[r0][c0] * N[r1][c1] - N[r0][c1] * N[r1][c0];
+    };
+    det = N[0][0] * minor(0, 0) - N[0][1] * minor(0, 1) + N[0][2] * minor(0, 2);
+    // (N^{-1})[want][b] = cofactor(b, want) / det
+    for (int b = 0; b < 3; ++b) adj[b] = (((b + want) & 1) ? -1 : 1) * minor(b, want);
+  }
+  for (int k = 0; k < K; ++k) {
+    i128 t = -k, pw = 1, num = 0;
+    for (int b = 0; b < m; ++b) {
+      num += adj[b] * pw;
+      pw *= t;
+    }
+    num *= factor;
+    i128 den = det;
+    if (den < 0) {
+      den = -den;
+      num = -num;
+    }
+    const i128 g = gcd128(num, den);
+    if (g > 1) {
+      num /= g;
+      den /= g;
+    }
+    if (iabs128(num) >= ((i128)1 << 53) || den >= ((i128)1 << 53)) return false;
+    w[k] = (double)(long long)num / (double)(long long)den;
+  }
+  return true;
+}
+
+struct Run {
+  int64_t first;       // global index of the run's first frame
+  int count;
+  const char* depth;   // plane of frame `first`, or NULL
+  int stage_slots;     // staging slots this run holds (0: caller memory)
+};
+
+struct TimerPair {
+  cudaEvent_t a, b;
+};
+
+// Adds the launches an entry point made to the process-wide counter.
+struct LaunchTally {
+  const int64_t* counter;
+  int64_t start;
+  explicit LaunchTally(const int64_t* c) : counter(c), start(*c) {}
+  ~LaunchTally() { g_launches.fetch_add(*counter - start); }
+};
+
+}  // namespace
+
+struct mf_stream {
+  mf_stream_desc d{};
+  int device = 0;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  double w[mf::kMaxHist] = {};
+  size_t plane_in = 0, plane_out = 0;  // bytes per depth plane / map plane
+
+  double* ring = nullptr;
+  int32_t* ring_bad = nullptr;
+  int64_t ring_cap = 0;
+  FrameRec* recs = nullptr;
+  int64_t rec_cap = 0;
+
+  double* pose_dev = nullptr;      // device staging of host poses
+  int64_t pose_dev_cap = 0;
+  double* pose_host = nullptr;     // pinned bounce buffer for host poses
+  int64_t pose_host_cap = 0;
+  cudaEvent_t pose_ev = nullptr;   // last upload from pose_host
+
+  char* stage = nullptr;           // device staging ring of depth planes
+  int64_t stage_slots = 0, stage_head = 0, stage_used = 0;
+  char* out_stage = nullptr;       // device staging of outputs bound for host
+  size_t out_stage_bytes = 0;
+  cudaEvent_t done_ev = nullptr;
+
+  int64_t emitted = 0, rendered = 0, pushes = 0, pushed_frames = 0;
+  std::deque<Run> runs;
+  int64_t launches = 0;
+  std::vector<TimerPair> timers, free_timers;
+  double map_ms = 0.0;
+  int64_t map_timed = 0;
+  int64_t device_bytes = 0;
+
+  void* dalloc(size_t bytes) {
+    void* p = nullptr;
+    if (d.dev_alloc) {
+      p = d.dev_alloc(bytes, d.alloc_ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+    if (p) device_bytes += (int64_t)bytes;
+    return p;
+  }
+  void dfree(void* p, size_t bytes) {
+    if (!p) return;
+    if (d.dev_free)
+      d.dev_free(p, d.alloc_ctx);
+    else
+      cudaFree(p);
+    device_bytes -= (int64_t)bytes;
+  }
+};
+
+namespace {
+
+int grow_ring(mf_stream* s, int64_t need) {
+  if (need <= s->ring_cap) return MF_OK;
+  const int64_t cap = pow2_at_least(std::max<int64_t>(need, 128));
+  double* ring = (double*)s->dalloc((size_t)cap * 12 * sizeof(double));
+  int32_t* bad = (int32_t*)s->dalloc((size_t)cap * sizeof(int32_t));
+  if (!ring || !bad) {
+    s->dfree(ring, (size_t)cap * 12 * sizeof(double));
+    s->dfree(bad, (size_t)cap * sizeof(int32_t));
+    return fail(MF_ERR_OOM, "pose history allocation failed");
+  }
+  if (s->ring && s->emitted > 0) {
+    const int64_t keep = std::min<int64_t>(s->emitted, s->d.window + s->d.smooth_len - 1);
+    MF_CUDA(mf::launch_ring_copy(s->ring, s->ring_bad, s->ring_cap - 1, ring, bad, cap - 1,
+                                 s->emitted - keep, (int)keep, s->st, &s->launches),
+            "history copy launch");
+  }
+  if (s->ring) {
+    MF_CUDA(cudaStreamSynchronize(s->st), "stream sync before freeing history");
+    s->dfree(s->ring, (size_t)s->ring_cap * 12 * sizeof(double));
+    s->dfree(s->ring_bad, (size_t)s->ring_cap * sizeof(int32_t));
+  }
+  s->ring = ring;
+  s->ring_bad = bad;
+  s->ring_cap = cap;
+  return MF_OK;
+}
+
+// Staging ring of depth planes for host-memory depth.  Grows (copying the
+// pending planes in order) when the pending planes plus `need` do not fit.
+int ensure_stage(mf_stream* s, int64_t need) {
+  if (s->stage_used + need <= s->stage_slots) return MF_OK;
+  const int64_t slots = std::max<int64_t>(s->stage_used + need, 2 * s->stage_slots);
+  char* buf = (char*)s->dalloc((size_t)slots * s->plane_in);
+  if (!buf) return fail(MF_ERR_OOM, "depth staging allocation failed");
+  // move pending planes to slots 0..used-1 and repoint their runs
+  int64_t moved = 0;
+  for (Run& r : s->runs) {
+    if (r.stage_slots == 0) continue;
+    MF_CUDA(cudaMemcpyAsync(buf + (size_t)moved * s->plane_in, r.depth,
+                            (size_t)r.count * s->plane_in, cudaMemcpyDeviceToDevice, s->st),
+            "staging move");
+    r.depth = buf + (size_t)moved * s->plane_in;
+    moved += r.count;
+  }
+  if (s->stage) {
+    MF_CUDA(cudaStreamSynchronize(s->st), "stream sync before freeing staging");
+    s->dfree(s->stage, (size_t)s->stage_slots * s->plane_in);
+  }
+  s->stage = buf;
+  s->stage_slots = slots;
+  s->stage_head = 0;
+  s->stage_used = moved;
+  return MF_OK;
+}
+
+int ensure_out_stage(mf_stream* s, size_t bytes) {
+  if (bytes <= s->out_stage_bytes) return MF_OK;
+  if (s->out_stage) {
+    MF_CUDA(cudaStreamSynchronize(s->st), "stream sync before freeing output staging");
+    s->dfree(s->out_stage, s->out_stage_bytes);
+    s->out_stage = nullptr;
+    s->out_stage_bytes = 0;
+  }
+  s->out_stage = (char*)s->dalloc(bytes);
+  if (!s->out_stage) return fail(MF_ERR_OOM, "output staging allocation failed");
+  s->out_stage_bytes = bytes;
+  return MF_OK;
+}
+
+int wait_event(cudaEvent_t ev, int64_t timeout_ns) {
+  const auto t0 = std::chrono::steady_clock::now();
+  int spins = 0;
+  for (;;) {
+    cudaError_t e = cudaEventQuery(ev);
+    if (e == cudaSuccess) return MF_OK;
+    if (e != cudaErrorNotReady) return fail(MF_ERR_CUDA, "event query", e);
+    if (timeout_ns >= 0) {
+      const auto ns = std::chrono::duration_cast<std::chrono::nanoseconds>(
+                          std::chrono::steady_clock::now() - t0)
+                          .count();
+      if (ns > timeout_ns) return fail(MF_ERR_TIMEOUT, "wait timed out");
+    }
+    if (++spins > 64)
+      std::this_thread::sleep_for(std::chrono::microseconds(20));
+    else
+      std::this_thread::yield();
+  }
+}
+
+int collect_timers(mf_stream* s) {
+  for (TimerPair& t : s->timers) {
+    MF_CUDA(cudaEventSynchronize(t.b), "timer sync");
+    float ms = 0.0f;
+    MF_CUDA(cudaEventElapsedTime(&ms, t.a, t.b), "timer elapsed");
+    s->map_ms += ms;
+    ++s->map_timed;
+    s->free_timers.push_back(t);
+  }
+  s->timers.clear();
+  return MF_OK;
+}
+
+int timer_pair(mf_stream* s, TimerPair* out) {
+  if (!s->free_timers.empty()) {
+    *out = s->free_timers.back();
+    s->free_timers.pop_back();
+    return MF_OK;
+  }
+  MF_CUDA(cudaEventCreate(&out->a), "event create");
+  MF_CUDA(cudaEventCreate(&out->b), "event create");
+  return MF_OK;
+}
+
+void destroy(mf_stream* s) {
+  if (s->st) cudaStreamSynchronize(s->st);
+  collect_timers(s);
+  for (TimerPair& t : s->free_timers) {
+    cudaEventDestroy(t.a);
+    cudaEventDestroy(t.b);
+  }
+  s->dfree(s->ring, (size_t)s->ring_cap * 12 * sizeof(double));
+  s->dfree(s->ring_bad, (size_t)s->ring_cap * sizeof(int32_t));
+  s->dfree(s->recs, (size_t)s->rec_cap * sizeof(FrameRec));
+  s->dfree(s->pose_dev, (size_t)s->pose_dev_cap * 12 * sizeof(double));
+  s->dfree(s->stage, (size_t)s->stage_slots * s->plane_in);
+  s->dfree(s->out_stage, s->out_stage_bytes);
+  if (s->pose_host) cudaFreeHost(s->pose_host);
+  if (s->pose_ev) cudaEventDestroy(s->pose_ev);
+  if (s->done_ev) cudaEventDestroy(s->done_ev);
+  if (s->own_stream && s->st) cudaStreamDestroy(s->st);
+  delete s;
+}
+
+int validate_desc(const mf_stream_desc* d) {
+  if (!d) return fail(MF_ERR_INVALID_ARG, "NULL descriptor");
+  if (d->width < 1 || d->height < 1 || d->width > MF_MAX_DIM || d->height > MF_MAX_DIM)
+    return fail(MF_ERR_INVALID_ARG, "width/height out of range");
+  if ((int64_t)d->width * d->height > 0x7fffffffLL)
+    return fail(MF_ERR_INVALID_ARG, "frame too large");
+  if (d->calib_width < 0 || d->calib_height < 0)
+    return fail(MF_ERR_INVALID_ARG, "negative calibration size");
+  if (d->window < 1 || d->window > MF_MAX_WINDOW)
+    return fail(MF_ERR_INVALID_ARG, "window must be 1..32");
+  if (d->mode != MF_MODE_ACCEL && d->mode != MF_MODE_HEADING)
+    return fail(MF_ERR_INVALID_ARG, "unknown mode");
+  if (d->smooth_len < (d->mode == MF_MODE_ACCEL ? 3 : 2))
+    return fail(MF_ERR_INVALID_ARG, "smooth_len too small for the mode");
+  if (d->window + d->smooth_len - 1 > MF_MAX_HISTORY)
+    return fail(MF_ERR_INVALID_ARG, "window + smooth_len - 1 exceeds 64");
+  if (d->pose_frame == MF_POSES_WORLD) {
+    if (d->overlap != 0) return fail(MF_ERR_INVALID_ARG, "overlap must be 0 for world poses");
+  } else if (d->pose_frame == MF_POSES_BATCH_LOCAL) {
+    if (d->overlap < 1) return fail(MF_ERR_INVALID_ARG, "batch-local poses need overlap >= 1");
+  } else {
+    return fail(MF_ERR_INVALID_ARG, "unknown pose frame");
+  }
+  for (int dt : {d->depth_dtype, d->map_dtype})
+    if (dt != MF_F32 && dt != MF_BF16 && dt != MF_F16)
+      return fail(MF_ERR_INVALID_ARG, "unknown dtype");
+  if (d->max_pending < 1 || d->max_pending > (1 << 24))
+    return fail(MF_ERR_INVALID_ARG, "max_pending out of range");
+  if (!(d->sigma_rel > 0.0) || !(d->s_lo > 0.0) || !(d->s_hi >= d->s_lo) ||
+      !(d->depth_ref_m > 0.0) || !std::isfinite(d->sigma_rel) || !std::isfinite(d->s_hi) ||
+      !std::isfinite(d->depth_ref_m))
+    return fail(MF_ERR_INVALID_ARG, "sigma_rel, s_lo, s_hi or depth_ref_m invalid");
+  if ((d->dev_alloc == nullptr) != (d->dev_free == nullptr))
+    return fail(MF_ERR_INVALID_ARG, "dev_alloc and dev_free must be given together");
+  return MF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void mf_stream_desc_init(mf_stream_desc* d) {
+  if (!d) return;
+  std::memset(d, 0, sizeof(*d));
+  d->window = 8;
+  d->smooth_len = 15;
+  d->mode = MF_MODE_ACCEL;
+  d->pose_frame = MF_POSES_WORLD;
+  d->depth_dtype = MF_F32;
+  d->map_dtype = MF_F32;
+  d->max_pending = 1024;
+  d->sigma_rel = 0.1;
+  d->s_lo = 0.25;
+  d->s_hi = 4.0;
+  d->depth_ref_m = 1.0;
+}
+
+int mf_open_stream(const mf_stream_desc* d, mf_stream** out) {
+  if (!out) return fail(MF_ERR_INVALID_ARG, "NULL output handle");
+  *out = nullptr;
+  int rc = validate_desc(d);
+  if (rc) return rc;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+    cudaGetLastError();
+    return fail(MF_ERR_NO_DEVICE, "no CUDA device");
+  }
+  mf_stream* s = new (std::nothrow) mf_stream();
+  if (!s) return fail(MF_ERR_OOM, "host allocation failed");
+  s->d = *d;
+  if (cudaGetDevice(&s->device) != cudaSuccess) {
+    delete s;
+    return fail(MF_ERR_NO_DEVICE, "cudaGetDevice failed");
+  }
+  if (!ls_weights(d->smooth_len, d->mode, s->w)) {
+    delete s;
+    return fail(MF_ERR_INVALID_ARG, "least-squares weights not representable");
+  }
+  s->plane_in = (size_t)d->width * d->height * dtype_size(d->depth_dtype);
+  s->plane_out = (size_t)d->width * d->height * dtype_size(d->map_dtype);
+  if (d->cuda_stream) {
+    s->st = (cudaStream_t)d->cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking) != cudaSuccess) {
+      delete s;
+      return fail(MF_ERR_CUDA, "stream creation failed");
+    }
+    s->own_stream = true;
+  }
+  if (cudaEventCreateWithFlags(&s->pose_ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->done_ev, cudaEventDisableTiming) != cudaSuccess) {
+    destroy(s);
+    return fail(MF_ERR_CUDA, "event creation failed");
+  }
+  s->rec_cap = pow2_at_least(d->max_pending);
+  s->recs = (FrameRec*)s->dalloc((size_t)s->rec_cap * sizeof(FrameRec));
+  if (!s->recs) {
+    destroy(s);
+    return fail(MF_ERR_OOM, "frame record allocation failed");
+  }
+  rc = grow_ring(s, d->window + d->smooth_len + 64);
+  if (rc) {
+    destroy(s);
+    return rc;
+  }
+  *out = s;
+  return MF_OK;
+}
+
+int mf_push_frames(mf_stream* s, int32_t n, const double* poses, const void* depth,
+                   const double* K) {
+  if (!s) return fail(MF_ERR_INVALID_ARG, "NULL stream");
+  if (n < 1 || !poses || !K) return fail(MF_ERR_INVALID_ARG, "n < 1 or NULL poses/K");
+  const bool local = s->d.pose_frame == MF_POSES_BATCH_LOCAL;
+  const int O = (local && s->pushes > 0) ? s->d.overlap : 0;
+  if (n <= O) return fail(MF_ERR_INVALID_ARG, "batch must hold more frames than the overlap");
+  for (int k = 0; k < 4; ++k)
+    if (!std::isfinite(K[k])) return fail(MF_ERR_INVALID_ARG, "non-finite intrinsics");
+  if (!(K[0] > 0.0) || !(K[1] > 0.0)) return fail(MF_ERR_INVALID_ARG, "fx, fy must be > 0");
+  const int n_emit = n - O;
+  if (s->emitted - s->rendered + n_emit > s->rec_cap || s->emitted - s->rendered + n_emit > s->d.max_pending)
+    return fail(MF_ERR_NOT_READY, "too many pending frames: call mf_get_maps first");
+  DeviceGuard guard(s->device);
+  LaunchTally tally(&s->launches);
+
+  const int hist = s->d.window + s->d.smooth_len - 1;
+  int rc = grow_ring(s, (int64_t)hist + n_emit + 1);
+  if (rc) return rc;
+
+  // Poses: device pointers are read in place; host poses go through a pinned
+  // bounce buffer so the caller may reuse its memory at once.
+  const double* pdev = poses;
+  if (!is_device_ptr(poses)) {
+    if ((int64_t)n > s->pose_dev_cap) {
+      const int64_t cap = pow2_at_least(std::max<int64_t>(n, 256));
+      double* nd = (double*)s->dalloc((size_t)cap * 12 * sizeof(double));
+      if (!nd) return fail(MF_ERR_OOM, "pose staging allocation failed");
+      if (s->pose_dev) {
+        MF_CUDA(cudaStreamSynchronize(s->st), "stream sync");
+        s->dfree(s->pose_dev, (size_t)s->pose_dev_cap * 12 * sizeof(double));
+      }
+      s->pose_dev = nd;
+      s->pose_dev_cap = cap;
+    }
+    MF_CUDA(cudaEventSynchronize(s->pose_ev), "pose upload wait");
+    if ((int64_t)n > s->pose_host_cap) {
+      if (s->pose_host) cudaFreeHost(s->pose_host);
+      s->pose_host = nullptr;
+      const int64_t cap = pow2_at_least(std::max<int64_t>(n, 256));
+      MF_CUDA(cudaMallocHost(&s->pose_host, (size_t)cap * 12 * sizeof(double)), "pinned alloc");
+      s->pose_host_cap = cap;
+    }
+    std::memcpy(s->pose_host, poses, (size_t)n * 12 * sizeof(double));
+    MF_CUDA(cudaMemcpyAsync(s->pose_dev, s->pose_host, (size_t)n * 12 * sizeof(double),
+                            cudaMemcpyHostToDevice, s->st),
+            "pose upload");
+    MF_CUDA(cudaEventRecord(s->pose_ev, s->st), "event record");
+    pdev = s->pose_dev;
+  }
+
+  // Depth: device planes are referenced; host planes are copied to staging.
+  std::vector<Run> new_runs;
+  if (depth) {
+    const char* dsrc = static_cast<const char*>(depth) + (size_t)O * s->plane_in;
+    if (is_device_ptr(depth)) {
+      new_runs.push_back(Run{s->emitted, n_emit, dsrc, 0});
+    } else {
+      rc = ensure_stage(s, n_emit);
+      if (rc) return rc;
+      int64_t done = 0;
+      while (done < n_emit) {
+        const int64_t slot = (s->stage_head + s->stage_used) % s->stage_slots;
+        const int64_t chunk = std::min<int64_t>(n_emit - done, s->stage_slots - slot);
+        char* dst = s->stage + (size_t)slot * s->plane_in;
+        MF_CUDA(cudaMemcpyAsync(dst, dsrc + (size_t)done * s->plane_in,
+                                (size_t)chunk * s->plane_in, cudaMemcpyHostToDevice, s->st),
+                "depth upload");
+        new_runs.push_back(Run{s->emitted + done, (int)chunk, dst, (int)chunk});
+        s->stage_used += chunk;
+        done += chunk;
+      }
+    }
+  } else {
+    new_runs.push_back(Run{s->emitted, n_emit, nullptr, 0});
+  }
+
+  mf::IngestParams ip{};
+  ip.in = pdev;
+  ip.n = n;
+  ip.first = O;
+  ip.anchor = O > 0 ? 1 : 0;
+  ip.ring = s->ring;
+  ip.ring_bad = s->ring_bad;
+  ip.ring_mask = s->ring_cap - 1;
+  ip.e0 = s->emitted;
+  MF_CUDA(mf::launch_ingest(ip, s->st, &s->launches), "ingest launch");
+
+  mf::PointsParams pp{};
+  pp.ring = s->ring;
+  pp.ring_bad = s->ring_bad;
+  pp.ring_mask = s->ring_cap - 1;
+  pp.recs = s->recs;
+  pp.rec_mask = s->rec_cap - 1;
+  pp.e0 = s->emitted;
+  pp.n_frames = n_emit;
+  pp.window = s->d.window;
+  pp.smooth_len = s->d.smooth_len;
+  pp.width = s->d.width;
+  pp.height = s->d.height;
+  pp.calib_width = s->d.calib_width;
+  pp.calib_height = s->d.calib_height;
+  for (int k = 0; k < 4; ++k) pp.K[k] = K[k];
+  pp.sigma_rel = s->d.sigma_rel;
+  pp.s_lo = s->d.s_lo;
+  pp.s_hi = s->d.s_hi;
+  for (int k = 0; k < mf::kMaxHist; ++k) pp.w[k] = k < s->d.smooth_len ? s->w[k] : 0.0;
+  MF_CUDA(mf::launch_points(pp, s->st, &s->launches), "points launch");
+
+  for (const Run& r : new_runs) s->runs.push_back(r);
+  s->emitted += n_emit;
+  s->pushed_frames += n;
+  ++s->pushes;
+  return MF_OK;
+}
+
+int mf_get_maps(mf_stream* s, int32_t max_frames, void* focus_map, void* guided_depth,
+                mf_frame_info* info, mf_motion_point* points, int32_t* n_out,
+                int64_t timeout_ns) {
+  if (!s || !n_out) return fail(MF_ERR_INVALID_ARG, "NULL stream or n_out");
+  *n_out = 0;
+  if (max_frames < 0) return fail(MF_ERR_INVALID_ARG, "max_frames < 0");
+  const int64_t take = std::min<int64_t>(max_frames, s->emitted - s->rendered);
+  if (take <= 0) return MF_OK;
+  DeviceGuard guard(s->device);
+  LaunchTally tally(&s->launches);
+
+  const bool m_host = focus_map && !is_device_ptr(focus_map);
+  const bool g_host = guided_depth && !is_device_ptr(guided_depth);
+  const bool i_host = info && !is_device_ptr(info);
+  const bool p_host = points && !is_device_ptr(points);
+  const size_t maps_bytes = (size_t)take * s->plane_out;
+  const size_t info_bytes = (size_t)take * sizeof(mf_frame_info);
+  const size_t pts_bytes = (size_t)take * s->d.window * sizeof(mf_motion_point);
+  auto round256 = [](size_t b) { return (b + 255) / 256 * 256; };
+  size_t need = 0;
+  if (m_host) need += round256(maps_bytes);
+  if (g_host) need += round256(maps_bytes);
+  if (i_host) need += round256(info_bytes);
+  if (p_host) need += round256(pts_bytes);
+  int rc = ensure_out_stage(s, need);
+  if (rc) return rc;
+  char* cur = s->out_stage;
+  auto place = [&](bool host, void* user, size_t bytes) -> char* {
+    if (!user) return nullptr;
+    if (!host) return static_cast<char*>(user);
+    char* p = cur;
+    cur += round256(bytes);
+    return p;
+  };
+  char* Md = place(m_host, focus_map, maps_bytes);
+  char* Gd = place(g_host, guided_depth, maps_bytes);
+  char* Id = place(i_host, info, info_bytes);
+  char* Pd = place(p_host, points, pts_bytes);
+
+  // one map launch per contiguous depth run
+  int64_t f = s->rendered;
+  int64_t done = 0;
+  const bool timed = (s->d.flags & MF_FLAG_TIME_KERNELS) != 0;
+  while (done < take) {
+    Run& r = s->runs.front();
+    const int64_t skip = f - r.first;
+    const int cnt = (int)std::min<int64_t>(r.count - skip, take - done);
+    mf::MapParams mp{};
+    mp.recs = s->recs;
+    mp.rec_mask = s->rec_cap - 1;
+    mp.f0 = f;
+    mp.n_frames = cnt;
+    mp.width = s->d.width;
+    mp.height = s->d.height;
+    mp.tile_h = mf::map_tile_h(s->d.width, s->d.height, s->d.window);
+    mp.tiles_x = (s->d.width + mf::kTileW - 1) / mf::kTileW;
+    mp.tiles_y = (s->d.height + mp.tile_h - 1) / mp.tile_h;
+    mp.depth = r.depth ? r.depth + (size_t)skip * s->plane_in : nullptr;
+    mp.M = Md ? Md + (size_t)done * s->plane_out : nullptr;
+    mp.G = Gd ? Gd + (size_t)done * s->plane_out : nullptr;
+    mp.d0 = (float)s->d.depth_ref_m;
+    TimerPair tp{};
+    if (timed) {
+      rc = timer_pair(s, &tp);
+      if (rc) return rc;
+      MF_CUDA(cudaEventRecord(tp.a, s->st), "event record");
+    }
+    MF_CUDA(mf::launch_map(mp, s->d.window, s->d.depth_dtype, s->d.map_dtype, s->st, &s->launches),
+            "map launch");
+    if (timed) {
+      MF_CUDA(cudaEventRecord(tp.b, s->st), "event record");
+      s->timers.push_back(tp);
+    }
+    f += cnt;
+    done += cnt;
+    if (skip + cnt == r.count) {
+      if (r.stage_slots) {
+        s->stage_head = (s->stage_head + r.stage_slots) % s->stage_slots;
+        s->stage_used -= r.stage_slots;
+      }
+      s->runs.pop_front();
+    }
+  }
+  mf::FinalizeParams fp{};
+  fp.recs = s->recs;
+  fp.rec_mask = s->rec_cap - 1;
+  fp.f0 = s->rendered;
+  fp.n_frames = (int)take;
+  fp.width = s->d.width;
+  fp.window = s->d.window;
+  fp.info = reinterpret_cast<mf_frame_info*>(Id);
+  fp.points = reinterpret_cast<mf_motion_point*>(Pd);
+  MF_CUDA(mf::launch_finalize(fp, s->st, &s->launches), "finalize launch");
+  s->rendered += take;
+  *n_out = (int32_t)take;
+
+  if (m_host || g_host || i_host || p_host) {
+    if (m_host)
+      MF_CUDA(cudaMemcpyAsync(focus_map, Md, maps_bytes, cudaMemcpyDeviceToHost, s->st), "D2H");
+    if (g_host)
+      MF_CUDA(cudaMemcpyAsync(guided_depth, Gd, maps_bytes, cudaMemcpyDeviceToHost, s->st), "D2H");
+    if (i_host) MF_CUDA(cudaMemcpyAsync(info, Id, info_bytes, cudaMemcpyDeviceToHost, s->st), "D2H");
+    if (p_host) MF_CUDA(cudaMemcpyAsync(points, Pd, pts_bytes, cudaMemcpyDeviceToHost, s->st), "D2H");
+    MF_CUDA(cudaEventRecord(s->done_ev, s->st), "event record");
+    return wait_event(s->done_ev, timeout_ns);
+  }
+  return MF_OK;
+}
+
+int mf_sync(mf_stream* s, int64_t timeout_ns) {
+  if (!s) return fail(MF_ERR_INVALID_ARG, "NULL stream");
+  DeviceGuard guard(s->device);
+  MF_CUDA(cudaEventRecord(s->done_ev, s->st), "event record");
+  return wait_event(s->done_ev, timeout_ns);
+}
+
+int mf_pending_frames(const mf_stream* s, int32_t* n) {
+  if (!s || !n) return fail(MF_ERR_INVALID_ARG, "NULL argument");
+  *n = (int32_t)(s->emitted - s->rendered);
+  return MF_OK;
+}
+
+int mf_reset_stream(mf_stream* s) {
+  if (!s) return fail(MF_ERR_INVALID_ARG, "NULL stream");
+  // Host bookkeeping only: every kernel and copy already enqueued reads and
+  // writes library memory in stream order before anything enqueued later.
+  s->emitted = s->rendered = s->pushes = 0;
+  s->runs.clear();
+  s->stage_head = s->stage_used = 0;
+  return MF_OK;
+}
+
+int mf_stream_stats(mf_stream* s, mf_stats* out) {
+  if (!s || !out) return fail(MF_ERR_INVALID_ARG, "NULL argument");
+  DeviceGuard guard(s->device);
+  int rc = collect_timers(s);
+  if (rc) return rc;
+  out->frames_pushed = s->pushed_frames;
+  out->frames_emitted = s->emitted;
+  out->frames_rendered = s->rendered;
+  out->kernel_launches = s->launches;
+  out->map_launches = s->map_timed;
+  out->map_kernel_ms = s->map_ms;
+  out->device_bytes = s->device_bytes;
+  return MF_OK;
+}
+
+int mf_close_stream(mf_stream* s) {
+  if (!s) return MF_OK;
+  DeviceGuard guard(s->device);
+  destroy(s);
+  return MF_OK;
+}
+
+const char* mf_status_string(int status) {
+  switch (status) {
+    case MF_OK: return "ok";
+    case MF_ERR_INVALID_ARG: return "invalid argument";
+    case MF_ERR_INVALID_POSE: return "invalid pose";
+    case MF_ERR_OOM: return "out of memory";
+    case MF_ERR_NOT_READY: return "not ready: too many pending frames";
+    case MF_ERR_TIMEOUT: return "timeout";
+    case MF_ERR_CUDA: return "CUDA error";
+    case MF_ERR_ADMISSION: return "admission refused";
+    case MF_ERR_NO_DEVICE: return "no CUDA device";
+  }
+  return "unknown status";
+}
+
+int mf_version(void) { return MF_VERSION; }
+
+int64_t mf_total_kernel_launches(void) { return g_launches.load(); }
+
+const char* mf_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,331 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O  # noqa: E402
+from synth import WalkerSpec, hd_stream, small_stream, walk  # noqa: E402
+from tests import parity  # noqa: E402
+from tests.posegen import rot_x, rot_y, trajectory  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TDT = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}
+
+
+@pytest.fixture(scope="module")
+def mf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    import paper_2601_07154_gb300 as m
+    return m
+
+
+def _mode(name):
+    return O.MODE_ACCEL if name == "accel" else O.MODE_HEADING
+
+
+def run_both(mf, poses, depth, K, width, height, window=8, smooth_len=15, mode="accel",
+             storage="f32", pushes=None, pose_frame="world", overlap=0, calib=None,
+             on_host=False, get_chunks=None):
+    """Run the same pushes through the GPU stream and the oracle."""
+    dev = torch.device("cuda", 0)
+    dt = TDT[storage]
+    s = mf.MotionFocusStream(width, height, window=window, smooth_len=smooth_len, mode=mode,
+                             pose_frame=pose_frame, overlap=overlap, depth_dtype=dt, map_dtype=dt,
+                             calib=calib, device=dev)
+    p = O.Params(width, height, window=window, smooth_len=smooth_len, mode=_mode(mode),
+                 pose_frame=O.POSES_BATCH_LOCAL if pose_frame == "batch_local" else O.POSES_WORLD,
+                 overlap=overlap, calib_width=calib[0] if calib else 0,
+                 calib_height=calib[1] if calib else 0)
+    ref = O.OracleStream(p)
+    pushes = pushes or [(0, len(poses))]
+    keep = []
+    for lo, hi in pushes:
+        P = np.ascontiguousarray(poses[lo:hi])
+        D = None
+        D64 = None
+        if depth is not None:
+            Dt = torch.from_numpy(np.ascontiguousarray(depth[lo:hi])).to(dt)
+            D64 = Dt.to(torch.float64).numpy()          # the values the kernel reads
+            D = Dt if on_host else Dt.to(dev)
+        Pt = P if on_host else torch.from_numpy(P).to(dev)
+        keep.append((Pt, D))
+        s.push(Pt, D, K)
+        ref.push(P, D64, K)
+    outs = []
+    if get_chunks:
+        for c in get_chunks:
+            outs.append(s.get_maps(c))
+    outs.append(s.get_maps())
+    M = torch.cat([o[0] for o in outs if o[0] is not None]).float().cpu().numpy()
+    G = torch.cat([o[1] for o in outs if o[1] is not None]).float().cpu().numpy()
+    info = np.concatenate([o[2] for o in outs])
+    pts = np.concatenate([o[3] for o in outs if o[3] is not None])
+    s.close()
+    return M, G, info, pts, ref
+
+
+def compare_all(M, G, info, pts, ref, K, storage="f32", maps=True):
+    assert len(info) == ref.n_emitted
+    intr = O.compensated_intrinsics(K, ref.p)
+    worst = 0.0
+    for n in range(ref.n_emitted):
+        rinfo, rp, Mr, Gr = ref.frame(n, full_maps=maps)
+        parity.check_frame(info[n], pts[n], rinfo, rp, intr, where=f"frame {n}")
+        if maps:
+            worst = max(worst, parity.check_map(M[n], Mr, storage, f"M frame {n}")[0])
+            if Gr is not None:
+                parity.check_map(G[n], Gr, storage, f"G frame {n}")
+            else:
+                assert not G[n].any()
+            if storage == "f32":
+                parity.check_argmax(info[n], Mr, rinfo["n_valid"], where=f"argmax {n}")
+    return worst
+
+
+# ---------------------------------------------------------------- configs --
+@pytest.mark.parametrize("mode", ["accel", "heading"])
+def test_small_stream_parity(mf, mode):
+    """320x240, 64 frames, window 8 (3 x 4 tiles with ragged right/bottom edges)."""
+    w = small_stream()
+    M, G, info, pts, ref = run_both(mf, w.poses, w.depth_stack(0, 64), w.K(), 320, 240,
+                                    window=8, smooth_len=15, mode=mode)
+    compare_all(M, G, info, pts, ref, w.K())
+    assert info["n_valid"].sum() > 300
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+def test_small_stream_16bit_storage(mf, storage):
+    w = small_stream()
+    M, G, info, pts, ref = run_both(mf, w.poses, w.depth_stack(0, 64), w.K(), 320, 240,
+                                    mode="heading", storage=storage)
+    compare_all(M, G, info, pts, ref, w.K(), storage=storage)
+
+
+def _accelerating_walk(n, width=320, seed=0):
+    """Forward acceleration with sway: ACCEL points land inside the frame."""
+    rng = np.random.default_rng(seed)
+    cs, rs = [], []
+    for k in range(n):
+        t = k / 30.0
+        cs.append(np.array([0.05 * math.sin(2.0 * t), 0.02 * math.sin(3.1 * t),
+                            1.0 * t + 0.6 * t * t]) + rng.normal(0, 1e-4, 3))
+        rs.append(rot_y(0.2 * math.sin(1.3 * t)) @ rot_x(0.05 * math.sin(4 * t)))
+    return trajectory(cs, rs)
+
+
+@pytest.mark.parametrize("window,smooth_len", [(8, 3), (16, 15), (32, 33), (5, 7), (1, 3)])
+def test_windows_in_frame_accel(mf, window, smooth_len):
+    poses = _accelerating_walk(80)
+    rng = np.random.default_rng(1)
+    depth = rng.uniform(0.2, 5.0, (80, 240, 320)).astype(np.float32)
+    K = np.array([260.0, 260.0, 160.0, 120.0])
+    M, G, info, pts, ref = run_both(mf, poses, depth, K, 320, 240, window=window,
+                                    smooth_len=smooth_len, mode="accel")
+    compare_all(M, G, info, pts, ref, K)
+    assert info["n_valid"][-1] == window and M[-1].max() > 0.05
+
+
+@pytest.mark.parametrize("width,height", [(333, 197), (130, 70), (4, 3), (1, 1), (129, 65)])
+def test_ragged_and_tiny_frames(mf, width, height):
+    poses = _accelerating_walk(30)
+    rng = np.random.default_rng(2)
+    depth = rng.uniform(0.2, 5.0, (30, height, width)).astype(np.float32)
+    K = np.array([0.8 * width + 1, 0.8 * width + 1, (width - 1) / 2, (height - 1) / 2])
+    M, G, info, pts, ref = run_both(mf, poses, depth, K, width, height, window=6,
+                                    smooth_len=5, mode="heading")
+    compare_all(M, G, info, pts, ref, K)
+
+
+def test_calibration_rescale(mf):
+    poses = _accelerating_walk(40)
+    K = np.array([520.0, 520.0, 319.5, 239.5])
+    M, G, info, pts, ref = run_both(mf, poses, None, K, 320, 240, window=8, smooth_len=5,
+                                    mode="heading", calib=(640, 480))
+    compare_all(M, G, info, pts, ref, K)
+
+
+# ------------------------------------------------------------ edge cases --
+def test_degenerate_constant_velocity_is_empty(mf):
+    cs = [np.array([0.01 * k, 0.0, 0.05 * k]) for k in range(40)]
+    poses = trajectory(cs, [rot_y(0.3)] * 40)
+    depth = np.ones((40, 48, 64), np.float32)
+    K = np.array([50.0, 50.0, 32.0, 24.0])
+    M, G, info, pts, ref = run_both(mf, poses, depth, K, 64, 48, window=8, smooth_len=15)
+    assert np.all(info["n_valid"] == 0) and np.all(info["status"] == O.FRAME_EMPTY)
+    assert not M.any() and not G.any()
+    assert np.all(info["argmax_x"] == -1)
+
+
+def test_bad_pose_and_invalid_depth(mf):
+    poses = _accelerating_walk(30)
+    poses[12, 0, 0] = 1.01
+    depth = np.full((30, 48, 64), 2.0, np.float32)
+    depth[:, 0, :] = 0.0
+    depth[:, 1, :] = np.nan
+    depth[:, 2, :] = np.inf
+    depth[:, 3, :] = -1.0
+    depth[:, 4, :] = 0.5
+    K = np.array([50.0, 50.0, 32.0, 24.0])
+    M, G, info, pts, ref = run_both(mf, poses, depth, K, 64, 48, window=4, smooth_len=3)
+    compare_all(M, G, info, pts, ref, K)
+    assert info["status"][12] == O.FRAME_BAD_POSE and info["valid_mask"][13] == 0b0011
+    assert not G[:, :4].any() and np.array_equal(G[:, 4], M[:, 4])
+
+
+def test_host_pointers_match_device_pointers(mf):
+    w = small_stream(n_frames=40)
+    d = w.depth_stack(0, 40)
+    a = run_both(mf, w.poses, d, w.K(), 320, 240, mode="heading")
+    b = run_both(mf, w.poses, d, w.K(), 320, 240, mode="heading", on_host=True)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    assert np.array_equal(a[2], b[2]) and np.array_equal(a[3], b[3])
+
+
+def test_split_pushes_and_partial_gets(mf):
+    """Frame accounting across pushes and partial mf_get_maps calls."""
+    w = small_stream(n_frames=60)
+    d = w.depth_stack(0, 60)
+    whole = run_both(mf, w.poses, d, w.K(), 320, 240, mode="heading")
+    split = run_both(mf, w.poses, d, w.K(), 320, 240, mode="heading",
+                     pushes=[(0, 1), (1, 17), (17, 18), (18, 60)], get_chunks=[5, 1, 20])
+    for a, b in zip(whole[:4], split[:4]):
+        assert np.array_equal(a, b)
+
+
+def test_batch_local_anchoring(mf):
+    """Section 2.2: batches in their own yaw+translation frames, overlap 4."""
+    world = walk(WalkerSpec(n_frames=90, seed=9, turns=True)).poses_w2c
+    rng = np.random.default_rng(3)
+    L, Ov = 24, 4
+    batches, start, b = [], 0, 0
+    local = []
+    while True:
+        hi = min(start + L, 90)
+        G = np.eye(4)
+        if b:
+            G[:3, :3] = rot_y(rng.uniform(-3, 3)) @ rot_x(0.1 * rng.normal())
+            G[:3, 3] = rng.normal(size=3) * 10
+        local.append(np.stack([(O.to4x4(world[k]) @ G)[:3] for k in range(start, hi)]))
+        batches.append((sum(len(x) for x in local[:-1]), sum(len(x) for x in local)))
+        if hi == 90:
+            break
+        start = hi - Ov
+        b += 1
+    poses = np.concatenate(local)
+    depth = np.ones((len(poses), 48, 64), np.float32) * 3.0
+    K = np.array([50.0, 50.0, 32.0, 24.0])
+    M, G, info, pts, ref = run_both(mf, poses, depth, K, 64, 48, window=8, smooth_len=7,
+                                    mode="heading", pushes=batches, pose_frame="batch_local",
+                                    overlap=Ov)
+    assert len(info) == 90
+    compare_all(M, G, info, pts, ref, K)
+
+
+def test_not_ready_and_empty_gets(mf):
+    dev = torch.device("cuda", 0)
+    s = mf.MotionFocusStream(16, 8, window=2, smooth_len=3, max_pending=10, device=dev)
+    P = torch.from_numpy(_accelerating_walk(12)).to(dev)
+    assert s.get_maps()[2].shape == (0,)
+    s.push(P[:6], None, (10.0, 10.0, 8.0, 4.0))
+    with pytest.raises(mf.MFError) as e:
+        s.push(P[6:12], None, (10.0, 10.0, 8.0, 4.0))
+    assert e.value.status == mf.MF_ERR_NOT_READY
+    M, G, info, pts = s.get_maps(4)
+    assert len(info) == 4 and s.pending() == 2
+    s.push(P[6:12], None, (10.0, 10.0, 8.0, 4.0))
+    assert s.pending() == 8 and not G.any()
+    s.close()
+
+
+def test_translation_scale_invariance_bit_exact_on_gpu(mf):
+    poses = _accelerating_walk(50)
+    scaled = poses.copy()
+    scaled[:, :, 3] *= 2.0 ** 7
+    depth = np.ones((50, 64, 96), np.float32)
+    K = np.array([80.0, 80.0, 48.0, 32.0])
+    a = run_both(mf, poses, depth, K, 96, 64, window=8, smooth_len=9)
+    b = run_both(mf, scaled, depth, K, 96, 64, window=8, smooth_len=9)
+    for x, y in zip(a[:4], b[:4]):
+        assert np.array_equal(x, y)
+
+
+def test_streams_alone_and_interleaved_identical(mf):
+    dev = torch.device("cuda", 0)
+    wa, wb = small_stream(seed=11, n_frames=30), small_stream(seed=12, n_frames=30)
+    da, db = (torch.from_numpy(w.depth_stack(0, 30)).to(dev) for w in (wa, wb))
+    pa, pb = (torch.from_numpy(w.poses).to(dev) for w in (wa, wb))
+
+    def alone(p, d, K):
+        s = mf.MotionFocusStream(320, 240, mode="heading", device=dev)
+        s.push(p, d, K)
+        r = s.get_maps()
+        s.close()
+        return r
+
+    ra, rb = alone(pa, da, wa.K()), alone(pb, db, wb.K())
+    sa = mf.MotionFocusStream(320, 240, mode="heading", device=dev)
+    sb = mf.MotionFocusStream(320, 240, mode="heading", device=dev)
+    for lo, hi in ((0, 10), (10, 30)):
+        sa.push(pa[lo:hi], da[lo:hi], wa.K())
+        sb.push(pb[lo:hi], db[lo:hi], wb.K())
+    xa, xb = sa.get_maps(), sb.get_maps()
+    for r, x in ((ra, xa), (rb, xb)):
+        assert torch.equal(r[0], x[0]) and torch.equal(r[1], x[1])
+        assert np.array_equal(r[2], x[2])
+    sa.close()
+    sb.close()
+
+
+# ---------------------------------------------------------- full workload --
+def test_hd_stream_full_size_sampled(mf):
+    """1920x1080 x 900 frames, window 16, FP32: one push and one get of all
+    frames (the launch configuration the benchmark times).  Every frame's
+    integers, focus and motion points are checked; maps on 256 sampled
+    pixels per frame plus each frame's argmax."""
+    w = hd_stream()
+    dev = torch.device("cuda", 0)
+    ring = torch.from_numpy(np.stack([w.depth(k) for k in range(w.ring)])).to(dev)
+    idx = torch.tensor([k % w.ring for k in range(w.n_frames)], device=dev)
+    depth = ring[idx].contiguous()
+    s = mf.MotionFocusStream(w.width, w.height, window=w.window, smooth_len=w.smooth_len,
+                             device=dev)
+    s.push(torch.from_numpy(w.poses).to(dev), depth, w.K())
+    M, G, info, pts = s.get_maps()
+    s.close()
+    ref = O.OracleStream(O.Params(w.width, w.height, window=w.window, smooth_len=w.smooth_len))
+    ref.push(w.poses, None, w.K())
+    intr = O.compensated_intrinsics(w.K(), ref.p)
+    rng = np.random.default_rng(5)
+    frames = range(w.n_frames)
+    ys = rng.integers(0, w.height, 256)
+    xs = rng.integers(0, w.width, 256)
+    yt, xt = torch.from_numpy(ys).to(dev), torch.from_numpy(xs).to(dev)
+    Ms = M[:, yt, xt].double().cpu().numpy()
+    Gs = G[:, yt, xt].double().cpu().numpy()
+    ringh = ring.double().cpu().numpy()
+    for n in frames:
+        rinfo, rp, _, _ = ref.frame(n, full_maps=False)
+        parity.check_frame(info[n], pts[n], rinfo, rp, intr, where=f"frame {n}")
+        Mr = O.focus_map(rp, w.width, w.height, xs, ys)
+        parity.check_map(Ms[n], Mr, where=f"M frame {n}")
+        Gr = O.guided_depth(Mr, ringh[n % w.ring][ys, xs], 1.0)
+        parity.check_map(Gs[n], Gr, where=f"G frame {n}")
+        if rinfo["n_valid"]:
+            ax, ay = int(info[n]["argmax_x"]), int(info[n]["argmax_y"])
+            m_at = O.focus_map(rp, w.width, w.height, np.array([ax]), np.array([ay]))[0]
+            assert abs(float(info[n]["map_max"]) - m_at) <= 1e-5 * m_at + 1e-10
+            assert float(M[n, ay, ax]) == float(info[n]["map_max"])
+    assert info["n_valid"].sum() > 5000
+    # three whole frames against the full FP64 map (values and argmax)
+    for n in (100, 451, 899):
+        rinfo, rp, _, _ = ref.frame(n, full_maps=False)
+        Mr = O.focus_map(rp, w.width, w.height)
+        parity.check_map(M[n].double().cpu().numpy(), Mr, where=f"full M frame {n}")
+        parity.check_argmax(info[n], Mr, rinfo["n_valid"], where=f"argmax {n}")
