@@ -253,6 +253,52 @@ int64_t mf_total_kernel_launches(void);
  * until the thread's next failing call. */
 const char* mf_last_error(void);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free rendering.  The paper has no counterpart to this entry
+ * point; it exists for callers that cannot let a library allocate device
+ * memory: real-time loops that must never meet a cudaMalloc (it can
+ * synchronise the device and has no latency bound), plugins running inside a
+ * host framework that owns all device memory through its own pool, and
+ * processes held to a fixed memory budget.
+ *
+ * It computes what a WORLD-pose stream would return for the last n_render of
+ * n_poses consecutive poses (frames 0 .. n_poses-1; the earlier poses serve
+ * as the window's history), with no mf_stream and no allocation: its
+ * scratch (pose copies, rigidity flags, per-frame records, about 560 KB) is
+ * a static device array inside libmf that every GPU loading the library
+ * holds until the process exits.  The caller passes and owns the inputs and
+ * the outputs.
+ *   d              stream descriptor: sizes, window, smooth_len, mode,
+ *                  dtypes, sigma/s/d0 parameters and cuda_stream are used;
+ *                  pose_frame must be MF_POSES_WORLD; dev_alloc, dev_free,
+ *                  max_pending and flags are ignored.  A NULL cuda_stream
+ *                  means the legacy default stream.
+ *   poses_w2c_3x4  n_poses x 12 FP64 world-to-camera poses (device memory)
+ *   depth          n_render depth planes of depth_dtype for frames
+ *                  n_poses-n_render .. n_poses-1 (device memory) or NULL
+ *   K              host pointer to fx, fy, cx, cy
+ *   focus_map, guided_depth
+ *                  n_render planes of map_dtype (device memory) or NULL
+ *   info           n_render mf_frame_info records (device memory) or NULL
+ * Limits: n_render <= MF_NOALLOC_MAX_FRAMES, n_poses <= MF_NOALLOC_MAX_POSES;
+ * larger sizes, host pointers or batch-local poses return
+ * MF_ERR_INVALID_ARG before any work is enqueued.  The call only enqueues
+ * kernels on cuda_stream; results are ready when that stream reaches them.
+ * It calls no cudaMalloc, cudaFree or other allocating routine.
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Every call on a device shares the one array and
+ * leaves its contents behind (each call rewrites all it reads), so calls whose
+ * work overlaps on the GPU race: issue them on one stream, or synchronise
+ * between them.
+ */
+#define MF_NOALLOC_MAX_FRAMES 256
+#define MF_NOALLOC_MAX_POSES (MF_NOALLOC_MAX_FRAMES + MF_MAX_HISTORY - 1)
+
+int mf_render_noalloc(const mf_stream_desc* d, int32_t n_poses, const double* poses_w2c_3x4,
+                      int32_t n_render, const void* depth, const double* K, void* focus_map,
+                      void* guided_depth, mf_frame_info* info);
+
 #ifdef __cplusplus
 }
 #endif

@@ -25,7 +25,9 @@ MF_FLAG_TIME_KERNELS = 1
 EXPORTED = ("mf_stream_desc_init", "mf_open_stream", "mf_push_frames", "mf_get_maps",
             "mf_sync", "mf_pending_frames", "mf_reset_stream", "mf_stream_stats",
             "mf_close_stream", "mf_status_string", "mf_version", "mf_total_kernel_launches",
-            "mf_last_error")
+            "mf_last_error", "mf_render_noalloc")
+MF_NOALLOC_MAX_FRAMES = 256
+MF_NOALLOC_MAX_POSES = MF_NOALLOC_MAX_FRAMES + 63
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
@@ -98,8 +100,11 @@ def _load():
     lib.mf_version.restype = ctypes.c_int
     lib.mf_total_kernel_launches.restype = i64
     lib.mf_last_error.restype = ctypes.c_char_p
+    lib.mf_render_noalloc.argtypes = [ctypes.POINTER(MFStreamDesc), i32, vp, i32, vp, vp, vp, vp,
+                                      vp]
     for name in ("mf_open_stream", "mf_push_frames", "mf_get_maps", "mf_sync",
-                 "mf_pending_frames", "mf_reset_stream", "mf_stream_stats", "mf_close_stream"):
+                 "mf_pending_frames", "mf_reset_stream", "mf_stream_stats", "mf_close_stream",
+                 "mf_render_noalloc"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -196,3 +201,10 @@ def mf_total_kernel_launches():
 
 def mf_last_error():
     return lib.mf_last_error().decode(errors="replace")
+
+
+def mf_render_noalloc(desc, n_poses, poses, n_render, depth, K, focus_map=None,
+                      guided_depth=None, info=None):
+    _check(lib.mf_render_noalloc(ctypes.byref(desc), int(n_poses), ptr(poses), int(n_render),
+                                 ptr(depth), ptr(K), ptr(focus_map), ptr(guided_depth), ptr(info)),
+           "mf_render_noalloc")

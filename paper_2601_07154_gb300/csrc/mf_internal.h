@@ -107,4 +107,10 @@ cudaError_t launch_ring_copy(const double* src, const int32_t* src_bad, int64_t 
 // Map-kernel tile height used by the plain path.
 int map_tile_h(int width, int height, int window);
 
+// Host helpers defined in mf_stream.cpp.
+bool host_ls_weights(int K, int mode, double* w);
+int host_validate_desc(const mf_stream_desc* d);
+int host_fail(int status, const char* what, cudaError_t e);
+void host_count_launches(int64_t n);
+
 }  // namespace mf

@@ -397,6 +397,14 @@ int validate_desc(const mf_stream_desc* d) {
 
 }  // namespace
 
+namespace mf {
+// Host helpers shared with the allocation-free entry point (mf_noalloc.cu).
+bool host_ls_weights(int K, int mode, double* w) { return ls_weights(K, mode, w); }
+int host_validate_desc(const mf_stream_desc* d) { return validate_desc(d); }
+int host_fail(int status, const char* what, cudaError_t e) { return fail(status, what, e); }
+void host_count_launches(int64_t n) { g_launches.fetch_add(n); }
+}  // namespace mf
+
 extern "C" {
 
 void mf_stream_desc_init(mf_stream_desc* d) {
