@@ -22,6 +22,8 @@
 #include <cuda_fp16.h>
 #include <math.h>
 
+#include <algorithm>
+
 #include "mf_internal.h"
 
 namespace mf {
@@ -286,6 +288,190 @@ __global__ void __launch_bounds__(kMapThreads) map_kernel(MapParams p) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Streaming variant for frames whose rows allow 4-pixel vector access (the
+// common case).  Persistent CTAs of 8 warps walk a list of units (frame, band
+// of up to 256 rows, group of 8 adjacent 128-column strips).  Per unit the
+// CTA builds the band's row factors once in shared memory (one barrier per
+// unit, none per row); each warp then owns one strip: it keeps its 4 columns'
+// factors for all N points in registers and streams the band's rows.  Depth
+// rows arrive through a per-warp ring of kStages cp.async stages (no
+// registers held by loads in flight), maps leave through 128-bit streaming
+// stores.  Per pixel and point the arithmetic is the same FMA chain, in the
+// same point order, as the tiled kernel above.
+namespace {
+
+constexpr int kStages = 8;     // depth rows in flight per warp
+constexpr int kBandMax = 256;  // rows per unit
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* dst, const void* src) {
+  if (BYTES == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src));
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(dst)), "l"(src));
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+template <typename T>
+__device__ __forceinline__ float4 unpack4(const uint4& raw);
+template <>
+__device__ __forceinline__ float4 unpack4<float>(const uint4& raw) {
+  return make_float4(__uint_as_float(raw.x), __uint_as_float(raw.y), __uint_as_float(raw.z),
+                     __uint_as_float(raw.w));
+}
+template <>
+__device__ __forceinline__ float4 unpack4<__nv_bfloat16>(const uint4& raw) {
+  uint2 r = make_uint2(raw.x, raw.y);
+  const float2 a = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&r.x));
+  const float2 c = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&r.y));
+  return make_float4(a.x, a.y, c.x, c.y);
+}
+template <>
+__device__ __forceinline__ float4 unpack4<__half>(const uint4& raw) {
+  uint2 r = make_uint2(raw.x, raw.y);
+  const float2 a = __half22float2(*reinterpret_cast<__half2*>(&r.x));
+  const float2 c = __half22float2(*reinterpret_cast<__half2*>(&r.y));
+  return make_float4(a.x, a.y, c.x, c.y);
+}
+
+}  // namespace
+
+template <int NMAX, typename TIn, typename TOut>
+__global__ void __launch_bounds__(kMapThreads, NMAX <= 16 ? 2 : 1)
+    map_stream_kernel(MapParams p, int band_h) {
+  extern __shared__ float4 smem4[];
+  float* Ey = reinterpret_cast<float*>(smem4);                      // [band_h][NMAX]
+  uint4* ring = reinterpret_cast<uint4*>(Ey + (size_t)band_h * NMAX);  // [8 warps][kStages][32]
+  __shared__ PointsSmem<NMAX> P;
+
+  constexpr int kInBytes = 4 * (int)sizeof(TIn);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int groups_x = (p.tiles_x + 7) / 8;
+  const int bands = (p.height + band_h - 1) / band_h;
+  const long long units = (long long)p.n_frames * bands * groups_x;
+  const size_t plane = (size_t)p.width * (size_t)p.height;
+  const bool has_depth = p.depth != nullptr;
+  uint4* my_ring = ring + (size_t)warp * kStages * 32;
+
+  for (long long u = blockIdx.x; u < units; u += gridDim.x) {
+    const int f = (int)(u / ((long long)bands * groups_x));
+    const int rem = (int)(u - (long long)f * bands * groups_x);
+    const int b = rem / groups_x, g = rem - b * groups_x;
+    FrameRec* rec = const_cast<FrameRec*>(p.recs) + ((p.f0 + f) & p.rec_mask);
+    __syncthreads();  // the previous unit is done with P and Ey
+    const int n = rec->n_valid;
+    const int nc = min(NMAX, (n + 3) & ~3);
+    const float inv_n = rec->inv_n;
+    if (tid < n) {
+      P.uhi[tid] = rec->ux_hi[tid];
+      P.ulo[tid] = rec->ux_lo[tid];
+      P.vhi[tid] = rec->vy_hi[tid];
+      P.vlo[tid] = rec->vy_lo[tid];
+      P.chi[tid] = rec->c_hi[tid];
+      P.clo[tid] = rec->c_lo[tid];
+    }
+    __syncthreads();
+    const int y0 = b * band_h;
+    const int rows = min(band_h, p.height - y0);
+    for (int r = warp; r < rows; r += kMapThreads / 32)
+      for (int i = lane; i < nc; i += 32)
+        Ey[r * NMAX + i] =
+            i < n ? gauss_factor((float)(y0 + r), P.vhi[i], P.vlo[i], P.chi[i], P.clo[i]) * inv_n
+                  : 0.0f;
+    const int x0 = (g * 8 + warp) * kTileW;
+    const int xc = x0 + lane * 4;
+    const bool col_ok = xc < p.width;
+    float2 ex01[NMAX], ex23[NMAX];
+#pragma unroll
+    for (int i = 0; i < NMAX; ++i) {
+      if (i < nc) {
+        float e0 = 0.f, e1 = 0.f, e2 = 0.f, e3 = 0.f;
+        if (i < n && col_ok) {
+          e0 = gauss_factor((float)(xc + 0), P.uhi[i], P.ulo[i], P.chi[i], P.clo[i]);
+          e1 = gauss_factor((float)(xc + 1), P.uhi[i], P.ulo[i], P.chi[i], P.clo[i]);
+          e2 = gauss_factor((float)(xc + 2), P.uhi[i], P.ulo[i], P.chi[i], P.clo[i]);
+          e3 = gauss_factor((float)(xc + 3), P.uhi[i], P.ulo[i], P.chi[i], P.clo[i]);
+        }
+        ex01[i] = make_float2(e0, e1);
+        ex23[i] = make_float2(e2, e3);
+      }
+    }
+    __syncthreads();  // Ey complete
+    if (x0 >= p.width) continue;  // warp-uniform: this strip lies past the frame
+
+    const size_t row0 = (size_t)f * plane + (size_t)y0 * p.width + xc;
+    const char* dsrc = has_depth ? static_cast<const char*>(p.depth) + row0 * sizeof(TIn) : nullptr;
+    const size_t dstride = (size_t)p.width * sizeof(TIn);
+    auto issue = [&](int r) {
+      if (r < rows && col_ok && has_depth)
+        cp_async<kInBytes>(my_ring + (r % kStages) * 32 + lane, dsrc + (size_t)r * dstride);
+      cp_async_commit();
+    };
+#pragma unroll
+    for (int s = 0; s < kStages - 1; ++s) issue(s);
+    float best = -1.0f;
+    unsigned bidx = 0;
+    for (int r = 0; r < rows; ++r) {
+      issue(r + kStages - 1);
+      cp_async_wait<kStages - 1>();
+      float4 dv = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (has_depth) dv = unpack4<TIn>(my_ring[(r % kStages) * 32 + lane]);
+      float2 a01 = make_float2(0.f, 0.f), a23 = make_float2(0.f, 0.f);
+      const float4* ey4 = reinterpret_cast<const float4*>(Ey + r * NMAX);
+#pragma unroll
+      for (int i = 0; i < NMAX; i += 4) {
+        if (i >= nc) break;
+        const float4 e = ey4[i >> 2];
+        a01 = ffma2(ex01[i + 0], e.x, a01);
+        a23 = ffma2(ex23[i + 0], e.x, a23);
+        a01 = ffma2(ex01[i + 1], e.y, a01);
+        a23 = ffma2(ex23[i + 1], e.y, a23);
+        a01 = ffma2(ex01[i + 2], e.z, a01);
+        a23 = ffma2(ex23[i + 2], e.z, a23);
+        a01 = ffma2(ex01[i + 3], e.w, a01);
+        a23 = ffma2(ex23[i + 3], e.w, a23);
+      }
+      if (!col_ok) continue;
+      const float4 m = make_float4(a01.x, a01.y, a23.x, a23.y);
+      const size_t idx = row0 + (size_t)r * p.width;
+      if (p.M) Px<TOut>::store4(p.M, idx, m);
+      if (p.G) {
+        float4 gv;
+        gv.x = m.x * depth_weight(dv.x, p.d0);
+        gv.y = m.y * depth_weight(dv.y, p.d0);
+        gv.z = m.z * depth_weight(dv.z, p.d0);
+        gv.w = m.w * depth_weight(dv.w, p.d0);
+        Px<TOut>::store4(p.G, idx, gv);
+      }
+      const float m4 = fmaxf(fmaxf(m.x, m.y), fmaxf(m.z, m.w));
+      if (m4 > best) {
+        best = m4;
+        const unsigned pix = (unsigned)((y0 + r) * p.width + xc);
+        bidx = m.x == m4 ? pix : (m.y == m4 ? pix + 1 : (m.z == m4 ? pix + 2 : pix + 3));
+      }
+    }
+    cp_async_wait<0>();
+    unsigned long long key =
+        best >= 0.0f ? ((unsigned long long)__float_as_uint(best) << 32) | (0xffffffffu - bidx) : 0ull;
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
+      key = k2 > key ? k2 : key;
+    }
+    if (lane == 0 && n > 0 && key) atomicMax(&rec->argmax_key, key);
+  }
+}
+
 int map_tile_h(int width, int height, int window) {
   (void)width;
   (void)window;
@@ -304,9 +490,27 @@ cudaError_t launch_typed(const MapParams& p, cudaStream_t st) {
   const bool vec = (p.width % 4) == 0 && aligned(p.depth, Px<TIn>::kAlign) &&
                    aligned(p.M, Px<TOut>::kAlign) && aligned(p.G, Px<TOut>::kAlign);
   if (vec) {
-    auto k = map_kernel<NMAX, TIn, TOut, true>;
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k<<<(unsigned)blocks, kMapThreads, smem, st>>>(p);
+    // streaming kernel: persistent grid of (SMs x resident CTAs)
+    const int bands = (p.height + kBandMax - 1) / kBandMax;
+    const int band_h = (p.height + bands - 1) / bands;
+    const size_t smem2 = (size_t)band_h * NMAX * 4 + (size_t)(kMapThreads / 32) * kStages * 32 * 16;
+    auto k = map_stream_kernel<NMAX, TIn, TOut>;
+    static int per_sm = -1, sms = 0;
+    if (per_sm < 0) {
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(kBandMax * NMAX * 4 + (kMapThreads / 32) * kStages * 32 * 16));
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kMapThreads,
+                                                    (size_t)kBandMax * NMAX * 4 +
+                                                        (kMapThreads / 32) * kStages * 32 * 16);
+      if (per_sm < 1) per_sm = 1;
+    }
+    const long long units = (long long)p.n_frames * ((p.height + band_h - 1) / band_h) *
+                            ((p.tiles_x + 7) / 8);
+    const long long grid = std::min<long long>(units, (long long)sms * per_sm);
+    k<<<(unsigned)grid, kMapThreads, smem2, st>>>(p, band_h);
   } else {
     auto k = map_kernel<NMAX, TIn, TOut, false>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
