@@ -291,18 +291,26 @@ __global__ void __launch_bounds__(kMapThreads) map_kernel(MapParams p) {
 // ---------------------------------------------------------------------------
 // Streaming variant for frames whose rows allow 4-pixel vector access (the
 // common case).  Persistent CTAs of 8 warps walk a list of units (frame, band
-// of up to 256 rows, group of 8 adjacent 128-column strips).  Per unit the
-// CTA builds the band's row factors once in shared memory (one barrier per
-// unit, none per row); each warp then owns one strip: it keeps its 4 columns'
-// factors for all N points in registers and streams the band's rows.  Depth
-// rows arrive through a per-warp ring of kStages cp.async stages (no
-// registers held by loads in flight), maps leave through 128-bit streaming
-// stores.  Per pixel and point the arithmetic is the same FMA chain, in the
-// same point order, as the tiled kernel above.
+// of up to 256 rows, group of 8 adjacent 128-column strips).  Per unit:
+//   * warp 0 keeps only the points whose Gaussian can reach the unit: a
+//     point whose largest column factor over the unit times its largest row
+//     factor (times 1/Z) is below 2^-40 contributes less than 2^-40 to every
+//     pixel of it, far inside the 1e-10 absolute floor of the map tolerance;
+//     the kept points stay in their original order;
+//   * the CTA builds the band's row factors once in shared memory (one
+//     barrier per unit, none per row);
+//   * each warp owns one strip: it keeps its 4 columns' factors for the kept
+//     points in registers and streams the band's rows two at a time (four
+//     independent FMA chains), depth arriving through a per-warp ring of
+//     kStages cp.async stages (no registers held by loads in flight), maps
+//     leaving through 128-bit streaming stores.
+// Per pixel and point the arithmetic is the same FMA chain, in the same point
+// order, as the tiled kernel above.
 namespace {
 
-constexpr int kStages = 8;     // depth rows in flight per warp
+constexpr int kStages = 6;     // depth rows in flight per warp
 constexpr int kBandMax = 256;  // rows per unit
+constexpr float kCullBelow = 9.094947017729282e-13f;  // 2^-40
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return static_cast<unsigned>(__cvta_generic_to_shared(p));
@@ -345,15 +353,48 @@ __device__ __forceinline__ float4 unpack4<__half>(const uint4& raw) {
   return make_float4(a.x, a.y, c.x, c.y);
 }
 
+// Two rows' N-term sums for one thread's 4 columns, points in order 0..nc-1.
+// NC > 0 fixes the trip count at compile time (all NMAX points kept).
+template <int NMAX, int NC>
+__device__ __forceinline__ void accum_two_rows(const float2* ex01, const float2* ex23,
+                                               const float* ey0, const float* ey1, int nc,
+                                               float2& a01, float2& a23, float2& b01, float2& b23) {
+  const float4* e0p = reinterpret_cast<const float4*>(ey0);
+  const float4* e1p = reinterpret_cast<const float4*>(ey1);
+#pragma unroll
+  for (int i = 0; i < NMAX; i += 4) {
+    if (NC == 0 && i >= nc) break;
+    const float4 e = e0p[i >> 2];
+    const float4 f = e1p[i >> 2];
+    a01 = ffma2(ex01[i + 0], e.x, a01);
+    a23 = ffma2(ex23[i + 0], e.x, a23);
+    b01 = ffma2(ex01[i + 0], f.x, b01);
+    b23 = ffma2(ex23[i + 0], f.x, b23);
+    a01 = ffma2(ex01[i + 1], e.y, a01);
+    a23 = ffma2(ex23[i + 1], e.y, a23);
+    b01 = ffma2(ex01[i + 1], f.y, b01);
+    b23 = ffma2(ex23[i + 1], f.y, b23);
+    a01 = ffma2(ex01[i + 2], e.z, a01);
+    a23 = ffma2(ex23[i + 2], e.z, a23);
+    b01 = ffma2(ex01[i + 2], f.z, b01);
+    b23 = ffma2(ex23[i + 2], f.z, b23);
+    a01 = ffma2(ex01[i + 3], e.w, a01);
+    a23 = ffma2(ex23[i + 3], e.w, a23);
+    b01 = ffma2(ex01[i + 3], f.w, b01);
+    b23 = ffma2(ex23[i + 3], f.w, b23);
+  }
+}
+
 }  // namespace
 
 template <int NMAX, typename TIn, typename TOut>
 __global__ void __launch_bounds__(kMapThreads, NMAX <= 16 ? 2 : 1)
     map_stream_kernel(MapParams p, int band_h) {
   extern __shared__ float4 smem4[];
-  float* Ey = reinterpret_cast<float*>(smem4);                      // [band_h][NMAX]
-  uint4* ring = reinterpret_cast<uint4*>(Ey + (size_t)band_h * NMAX);  // [8 warps][kStages][32]
+  float* Ey = reinterpret_cast<float*>(smem4);                            // [band_h][NMAX]
+  uint4* ring = reinterpret_cast<uint4*>(Ey + (size_t)band_h * NMAX);     // [8][kStages][32]
   __shared__ PointsSmem<NMAX> P;
+  __shared__ int s_kept;
 
   constexpr int kInBytes = 4 * (int)sizeof(TIn);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -369,35 +410,71 @@ __global__ void __launch_bounds__(kMapThreads, NMAX <= 16 ? 2 : 1)
     const int rem = (int)(u - (long long)f * bands * groups_x);
     const int b = rem / groups_x, g = rem - b * groups_x;
     FrameRec* rec = const_cast<FrameRec*>(p.recs) + ((p.f0 + f) & p.rec_mask);
-    __syncthreads();  // the previous unit is done with P and Ey
-    const int n = rec->n_valid;
-    const int nc = min(NMAX, (n + 3) & ~3);
-    const float inv_n = rec->inv_n;
-    if (tid < n) {
-      P.uhi[tid] = rec->ux_hi[tid];
-      P.ulo[tid] = rec->ux_lo[tid];
-      P.vhi[tid] = rec->vy_hi[tid];
-      P.vlo[tid] = rec->vy_lo[tid];
-      P.chi[tid] = rec->c_hi[tid];
-      P.clo[tid] = rec->c_lo[tid];
-    }
-    __syncthreads();
     const int y0 = b * band_h;
     const int rows = min(band_h, p.height - y0);
+    const int gx0 = g * 8 * kTileW;
+    const int gx1 = min(p.width, gx0 + 8 * kTileW) - 1;
+    const int x0 = gx0 + warp * kTileW;
+    const int xc = x0 + lane * 4;
+    const bool col_ok = xc < p.width;
+    const size_t row0 = (size_t)f * plane + (size_t)y0 * p.width + xc;
+    const char* dsrc = has_depth ? static_cast<const char*>(p.depth) + row0 * sizeof(TIn) : nullptr;
+    const size_t dstride = (size_t)p.width * sizeof(TIn);
+    auto issue = [&](int r) {
+      if (r < rows && col_ok && has_depth)
+        cp_async<kInBytes>(my_ring + (r % kStages) * 32 + lane, dsrc + (size_t)r * dstride);
+      cp_async_commit();
+    };
+    // The first depth rows are requested before the unit's set-up, so the
+    // copies are in flight while the factors are computed.  Each warp's ring
+    // is its own; the previous unit drained it.
+#pragma unroll
+    for (int s = 0; s < kStages - 2; ++s) issue(s);
+    __syncthreads();  // the previous unit is done with P and Ey
+    const int n = rec->n_valid;
+    const float inv_n = rec->inv_n;
+    if (warp == 0) {
+      bool keep = false;
+      float uh = 0.f, ul = 0.f, vh = 0.f, vl = 0.f, ch = 0.f, cl = 0.f;
+      if (lane < n) {
+        uh = rec->ux_hi[lane];
+        ul = rec->ux_lo[lane];
+        vh = rec->vy_hi[lane];
+        vl = rec->vy_lo[lane];
+        ch = rec->c_hi[lane];
+        cl = rec->c_lo[lane];
+        // the factors peak at the unit's pixel nearest (u, v)
+        const float xn = fminf(fmaxf(rintf(uh + ul), (float)gx0), (float)gx1);
+        const float yn = fminf(fmaxf(rintf(vh + vl), (float)y0), (float)(y0 + rows - 1));
+        const float peak = gauss_factor(xn, uh, ul, ch, cl) * gauss_factor(yn, vh, vl, ch, cl);
+        keep = peak * inv_n >= kCullBelow;
+      }
+      const unsigned mask = __ballot_sync(0xffffffffu, keep);
+      if (keep) {
+        const int pos = __popc(mask & ((1u << lane) - 1u));
+        P.uhi[pos] = uh;
+        P.ulo[pos] = ul;
+        P.vhi[pos] = vh;
+        P.vlo[pos] = vl;
+        P.chi[pos] = ch;
+        P.clo[pos] = cl;
+      }
+      if (lane == 0) s_kept = __popc(mask);
+    }
+    __syncthreads();
+    const int nk = s_kept;
+    const int nc = min(NMAX, (nk + 3) & ~3);
     for (int r = warp; r < rows; r += kMapThreads / 32)
       for (int i = lane; i < nc; i += 32)
         Ey[r * NMAX + i] =
-            i < n ? gauss_factor((float)(y0 + r), P.vhi[i], P.vlo[i], P.chi[i], P.clo[i]) * inv_n
-                  : 0.0f;
-    const int x0 = (g * 8 + warp) * kTileW;
-    const int xc = x0 + lane * 4;
-    const bool col_ok = xc < p.width;
+            i < nk ? gauss_factor((float)(y0 + r), P.vhi[i], P.vlo[i], P.chi[i], P.clo[i]) * inv_n
+                   : 0.0f;
     float2 ex01[NMAX], ex23[NMAX];
 #pragma unroll
     for (int i = 0; i < NMAX; ++i) {
       if (i < nc) {
         float e0 = 0.f, e1 = 0.f, e2 = 0.f, e3 = 0.f;
-        if (i < n && col_ok) {
+        if (i < nk && col_ok) {
           e0 = gauss_factor((float)(xc + 0), P.uhi[i], P.ulo[i], P.chi[i], P.clo[i]);
           e1 = gauss_factor((float)(xc + 1), P.uhi[i], P.ulo[i], P.chi[i], P.clo[i]);
           e2 = gauss_factor((float)(xc + 2), P.uhi[i], P.ulo[i], P.chi[i], P.clo[i]);
@@ -409,40 +486,9 @@ __global__ void __launch_bounds__(kMapThreads, NMAX <= 16 ? 2 : 1)
     }
     __syncthreads();  // Ey complete
     if (x0 >= p.width) continue;  // warp-uniform: this strip lies past the frame
-
-    const size_t row0 = (size_t)f * plane + (size_t)y0 * p.width + xc;
-    const char* dsrc = has_depth ? static_cast<const char*>(p.depth) + row0 * sizeof(TIn) : nullptr;
-    const size_t dstride = (size_t)p.width * sizeof(TIn);
-    auto issue = [&](int r) {
-      if (r < rows && col_ok && has_depth)
-        cp_async<kInBytes>(my_ring + (r % kStages) * 32 + lane, dsrc + (size_t)r * dstride);
-      cp_async_commit();
-    };
-#pragma unroll
-    for (int s = 0; s < kStages - 1; ++s) issue(s);
     float best = -1.0f;
     unsigned bidx = 0;
-    for (int r = 0; r < rows; ++r) {
-      issue(r + kStages - 1);
-      cp_async_wait<kStages - 1>();
-      float4 dv = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (has_depth) dv = unpack4<TIn>(my_ring[(r % kStages) * 32 + lane]);
-      float2 a01 = make_float2(0.f, 0.f), a23 = make_float2(0.f, 0.f);
-      const float4* ey4 = reinterpret_cast<const float4*>(Ey + r * NMAX);
-#pragma unroll
-      for (int i = 0; i < NMAX; i += 4) {
-        if (i >= nc) break;
-        const float4 e = ey4[i >> 2];
-        a01 = ffma2(ex01[i + 0], e.x, a01);
-        a23 = ffma2(ex23[i + 0], e.x, a23);
-        a01 = ffma2(ex01[i + 1], e.y, a01);
-        a23 = ffma2(ex23[i + 1], e.y, a23);
-        a01 = ffma2(ex01[i + 2], e.z, a01);
-        a23 = ffma2(ex23[i + 2], e.z, a23);
-        a01 = ffma2(ex01[i + 3], e.w, a01);
-        a23 = ffma2(ex23[i + 3], e.w, a23);
-      }
-      if (!col_ok) continue;
+    auto emit = [&](const float2& a01, const float2& a23, const float4& dv, int r) {
       const float4 m = make_float4(a01.x, a01.y, a23.x, a23.y);
       const size_t idx = row0 + (size_t)r * p.width;
       if (p.M) Px<TOut>::store4(p.M, idx, m);
@@ -460,6 +506,30 @@ __global__ void __launch_bounds__(kMapThreads, NMAX <= 16 ? 2 : 1)
         const unsigned pix = (unsigned)((y0 + r) * p.width + xc);
         bidx = m.x == m4 ? pix : (m.y == m4 ? pix + 1 : (m.z == m4 ? pix + 2 : pix + 3));
       }
+    };
+    // Rows r and r+1 per iteration: the ring slots of rows r-2 and r-1 were
+    // consumed by the previous iteration, so rows r+kStages-2 and
+    // r+kStages-1 can be requested before rows r, r+1 are read.
+    for (int r = 0; r < rows; r += 2) {
+      issue(r + kStages - 2);
+      issue(r + kStages - 1);
+      cp_async_wait<kStages - 2>();
+      const bool two = r + 1 < rows;
+      float4 d0v = make_float4(0.f, 0.f, 0.f, 0.f), d1v = d0v;
+      if (has_depth) {
+        d0v = unpack4<TIn>(my_ring[(r % kStages) * 32 + lane]);
+        if (two) d1v = unpack4<TIn>(my_ring[((r + 1) % kStages) * 32 + lane]);
+      }
+      float2 a01 = make_float2(0.f, 0.f), a23 = a01, b01 = a01, b23 = a01;
+      const float* ey0 = Ey + r * NMAX;
+      const float* ey1 = Ey + (two ? r + 1 : r) * NMAX;
+      if (nc == NMAX)
+        accum_two_rows<NMAX, NMAX>(ex01, ex23, ey0, ey1, nc, a01, a23, b01, b23);
+      else
+        accum_two_rows<NMAX, 0>(ex01, ex23, ey0, ey1, nc, a01, a23, b01, b23);
+      if (!col_ok) continue;
+      emit(a01, a23, d0v, r);
+      if (two) emit(b01, b23, d1v, r + 1);
     }
     cp_async_wait<0>();
     unsigned long long key =
