@@ -214,6 +214,9 @@ def run_gpu(args):
         ms = float(t.item())
     value = frames * args.steps * world / (ms / 1000.0)
 
+    prec = None
+    if rank == 0 and not args.no_precision:
+        prec = run_precision(torch, mf, w, poses, depth, dev, args, value / world)
     e2e = None
     if rank == 0 and not args.no_e2e:
         del M, G
@@ -239,11 +242,56 @@ def run_gpu(args):
                          "algorithmic_bytes_per_launch": frames * FRAME_BYTES,
                          "launch_ms": round(map_ms, 4)},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+            "precision": prec,
         }
         print(json.dumps(rec), flush=True)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def run_precision(torch, mf, w, poses, depth, dev, args, f32_value):
+    """The same workload with 16-bit depth and map storage (FP32 arithmetic)."""
+    out = {}
+    frames = int(depth.shape[0])
+    steps = max(10, min(args.steps, 100))
+    Kh = np.ascontiguousarray(w.K())
+    for name, dt in (("bf16", torch.bfloat16), ("f16", torch.float16)):
+        d16 = depth.to(dt)
+        M = torch.empty((frames, HEIGHT, WIDTH), dtype=dt, device=dev)
+        G = torch.empty_like(M)
+        info = torch.empty(frames * 64, dtype=torch.uint8, device=dev)
+        stream = torch.cuda.Stream(dev)
+        s = mf.MotionFocusStream(WIDTH, HEIGHT, window=WINDOW, smooth_len=SMOOTH, device=dev,
+                                 cuda_stream=stream, time_kernels=True, depth_dtype=dt,
+                                 map_dtype=dt)
+        h = s.handle
+
+        def step():
+            mf.mf_reset_stream(h)
+            mf.mf_push_frames(h, frames, poses, d16, Kh)
+            mf.mf_get_maps(h, frames, M, G, info, None)
+
+        for _ in range(args.warmup):
+            step()
+        stream.synchronize()
+        s0 = s.stats()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(steps):
+            step()
+        ev1.record(stream)
+        ev1.synchronize()
+        s1 = s.stats()
+        ms = ev0.elapsed_time(ev1) / steps
+        map_ms = (s1.map_kernel_ms - s0.map_kernel_ms) / max(1, s1.map_launches - s0.map_launches)
+        fps = frames / (ms / 1000.0)
+        out[name] = {"value": round(fps, 2), "unit": "frames/s", "steps": steps,
+                     "map_gbs": round(frames * WIDTH * HEIGHT * 6 / (map_ms / 1000.0) / 1e9, 1),
+                     "bytes_per_px": 6, "gain_vs_f32": round(fps / f32_value, 3)}
+        s.close()
+        del d16, M, G
+    return out
 
 
 def run_e2e(torch, mf, w, depth_dev, dev, args):
@@ -353,6 +401,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--frames", type=int, default=FRAMES,
                     help="frames per step (default: the full 900-frame workload; "
                          "smaller values only for profiling captures)")

@@ -108,6 +108,36 @@ def test_small_stream_16bit_storage(mf, storage):
     compare_all(M, G, info, pts, ref, w.K(), storage=storage)
 
 
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+def test_16bit_storage_error_report(mf, storage):
+    """Per-output error of 16-bit storage against the FP64 oracle (printed).
+
+    The bound is the storage format's rounding on top of the FP32 tolerance.
+    """
+    import json
+    w = small_stream()
+    stats = {}
+    for mode in ("accel", "heading"):
+        M, G, info, pts, ref = run_both(mf, w.poses, w.depth_stack(0, 64), w.K(), 320, 240,
+                                        mode=mode, storage=storage)
+        errs = {"M": [], "G": []}
+        rels = {"M": [], "G": []}
+        for n in range(ref.n_emitted):
+            _, _, Mr, Gr = ref.frame(n)
+            for key, got, r in (("M", M[n], Mr), ("G", G[n], Gr)):
+                e = np.abs(got.astype(np.float64) - r)
+                errs[key].append(e)
+                big = r > 1e-6
+                rels[key].append(e[big] / r[big])
+                assert np.all(e <= parity.map_tol(r, storage)), (mode, key, n)
+        for key in ("M", "G"):
+            e = np.concatenate([x.ravel() for x in errs[key]])
+            rr = np.concatenate([x.ravel() for x in rels[key]])
+            stats[f"{mode}_{key}"] = {"max_abs": float(e.max()), "mean_abs": float(e.mean()),
+                                      "max_rel": float(rr.max()), "mean_rel": float(rr.mean())}
+    print("\nSTORAGE_ERROR", storage, json.dumps(stats))
+
+
 def _accelerating_walk(n, width=320, seed=0):
     """Forward acceleration with sway: ACCEL points land inside the frame."""
     rng = np.random.default_rng(seed)
