@@ -35,7 +35,8 @@ WIDTH, HEIGHT, FRAMES, WINDOW, SMOOTH = 1920, 1080, 900, 16, 15
 BYTES_PER_PX = 12  # depth read + focus map write + guided depth write (FP32)
 FRAME_BYTES = WIDTH * HEIGHT * BYTES_PER_PX
 PROFILE = os.path.join(ROOT, "profiles", "map_kernel_1080p_f32.txt")
-MAP_SRC = os.path.join(ROOT, "paper_2601_07154_gb300", "csrc", "mf_map_kernel.cu")
+MAP_SRC = [os.path.join(ROOT, "paper_2601_07154_gb300", "csrc", f)
+           for f in ("mf_map_kernel.cu", "mf_map_unit.cuh")]
 
 
 def env_int(name, default):
@@ -62,13 +63,21 @@ def hbm_peak():
         return 6800.0, "fallback"
 
 
+def map_source_hash():
+    h = hashlib.sha256()
+    for f in MAP_SRC:
+        if os.path.exists(f):
+            h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
 def profiled_traffic(frames):
     """DRAM bytes per launch from the committed ncu summary, if it matches the source."""
     try:
         text = open(PROFILE).read()
     except OSError:
         return None
-    src_hash = hashlib.sha256(open(MAP_SRC, "rb").read()).hexdigest()[:16]
+    src_hash = map_source_hash()
     vals = {}
     for line in text.splitlines():
         if ":" in line:

@@ -18,52 +18,13 @@
 // (u is split into a hi part on a 2^-8 grid plus a lo part) and a float pair
 // for c, so its relative error stays near one FP32 rounding; expf (full
 // precision) then costs at most 2 ulp per factor.
-#include <cuda_bf16.h>
-#include <cuda_fp16.h>
-#include <math.h>
-
 #include <algorithm>
 
-#include "mf_internal.h"
+#include "mf_map_unit.cuh"
 
 namespace mf {
 
 namespace {
-
-template <int NMAX>
-struct PointsSmem {
-  float uhi[NMAX], ulo[NMAX], vhi[NMAX], vlo[NMAX], chi[NMAX], clo[NMAX];
-};
-
-// exp(-(q - hi - lo)^2 * (chi + clo)) for an integer-valued q.
-__device__ __forceinline__ float gauss_factor(float q, float hi, float lo, float chi, float clo) {
-  const float dh = q - hi;                 // exact (hi on a 2^-8 grid, |q|, |hi| < 2^15)
-  const float p2 = dh * dh;
-  const float e2 = fmaf(dh, dh, -p2);      // dh^2 = p2 + e2 exactly
-  float qq = fmaf(-2.0f * dh, lo, e2);     // (dh - lo)^2 = p2 + qq
-  qq = fmaf(lo, lo, qq);
-  const float t1 = fmaf(clo, p2, chi * qq);
-  const float a = fmaf(chi, p2, t1);
-  return expf(-a);
-}
-
-__device__ __forceinline__ float2 ffma2(float2 a, float b, float2 c) {
-  float2 d;
-  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
-      "mov.b64 ra, {%2, %3};\n\t"
-      "mov.b64 rb, {%4, %4};\n\t"
-      "mov.b64 rc, {%5, %6};\n\t"
-      "fma.rn.f32x2 rd, ra, rb, rc;\n\t"
-      "mov.b64 {%0, %1}, rd;\n\t}"
-      : "=f"(d.x), "=f"(d.y)
-      : "f"(a.x), "f"(a.y), "f"(b), "f"(c.x), "f"(c.y));
-  return d;
-}
-
-__device__ __forceinline__ float depth_weight(float D, float d0) {
-  // min(1, d0 / D) for finite D > 0, else 0 (NaN fails both comparisons)
-  return (D > 0.0f && D <= 3.402823466e38f) ? fminf(1.0f, __fdividef(d0, D)) : 0.0f;
-}
 
 // Storage types: 4 consecutive pixels per access.
 template <typename T>
@@ -71,7 +32,6 @@ struct Px;
 
 template <>
 struct Px<float> {
-  static constexpr int kAlign = 16;
   static __device__ __forceinline__ float4 load4(const void* b, size_t i) {
     return __ldcs(reinterpret_cast<const float4*>(static_cast<const float*>(b) + i));
   }
@@ -88,7 +48,6 @@ struct Px<float> {
 
 template <>
 struct Px<__nv_bfloat16> {
-  static constexpr int kAlign = 8;
   static __device__ __forceinline__ float4 load4(const void* b, size_t i) {
     uint2 r = __ldcs(reinterpret_cast<const uint2*>(static_cast<const __nv_bfloat16*>(b) + i));
     const float2 a = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&r.x));
@@ -113,7 +72,6 @@ struct Px<__nv_bfloat16> {
 
 template <>
 struct Px<__half> {
-  static constexpr int kAlign = 8;
   static __device__ __forceinline__ float4 load4(const void* b, size_t i) {
     uint2 r = __ldcs(reinterpret_cast<const uint2*>(static_cast<const __half*>(b) + i));
     const float2 a = __half22float2(*reinterpret_cast<__half2*>(&r.x));
@@ -289,256 +247,38 @@ __global__ void __launch_bounds__(kMapThreads) map_kernel(MapParams p) {
 }
 
 // ---------------------------------------------------------------------------
-// Streaming variant for frames whose rows allow 4-pixel vector access (the
-// common case).  Persistent CTAs of 8 warps walk a list of units (frame, band
-// of up to 256 rows, group of 8 adjacent 128-column strips).  Per unit:
-//   * warp 0 keeps only the points whose Gaussian can reach the unit: a
-//     point whose largest column factor over the unit times its largest row
-//     factor (times 1/Z) is below 2^-40 contributes less than 2^-40 to every
-//     pixel of it, far inside the 1e-10 absolute floor of the map tolerance;
-//     the kept points stay in their original order;
-//   * the CTA builds the band's row factors once in shared memory (one
-//     barrier per unit, none per row);
-//   * each warp owns one strip: it keeps its 4 columns' factors for the kept
-//     points in registers and streams the band's rows two at a time (four
-//     independent FMA chains), depth arriving through a per-warp ring of
-//     kStages cp.async stages (no registers held by loads in flight), maps
-//     leaving through 128-bit streaming stores.
-// Per pixel and point the arithmetic is the same FMA chain, in the same point
-// order, as the tiled kernel above.
-namespace {
-
-constexpr int kStages = 6;     // depth rows in flight per warp
-constexpr int kBandMax = 256;  // rows per unit
-constexpr float kCullBelow = 9.094947017729282e-13f;  // 2^-40
-
-__device__ __forceinline__ unsigned smem_u32(const void* p) {
-  return static_cast<unsigned>(__cvta_generic_to_shared(p));
-}
-
-template <int BYTES>
-__device__ __forceinline__ void cp_async(void* dst, const void* src) {
-  if (BYTES == 16)
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src));
-  else
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(dst)), "l"(src));
-}
-
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
-}
-
-template <typename T>
-__device__ __forceinline__ float4 unpack4(const uint4& raw);
-template <>
-__device__ __forceinline__ float4 unpack4<float>(const uint4& raw) {
-  return make_float4(__uint_as_float(raw.x), __uint_as_float(raw.y), __uint_as_float(raw.z),
-                     __uint_as_float(raw.w));
-}
-template <>
-__device__ __forceinline__ float4 unpack4<__nv_bfloat16>(const uint4& raw) {
-  uint2 r = make_uint2(raw.x, raw.y);
-  const float2 a = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&r.x));
-  const float2 c = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&r.y));
-  return make_float4(a.x, a.y, c.x, c.y);
-}
-template <>
-__device__ __forceinline__ float4 unpack4<__half>(const uint4& raw) {
-  uint2 r = make_uint2(raw.x, raw.y);
-  const float2 a = __half22float2(*reinterpret_cast<__half2*>(&r.x));
-  const float2 c = __half22float2(*reinterpret_cast<__half2*>(&r.y));
-  return make_float4(a.x, a.y, c.x, c.y);
-}
-
-// Two rows' N-term sums for one thread's 4 columns, points in order 0..nc-1.
-// NC > 0 fixes the trip count at compile time (all NMAX points kept).
-template <int NMAX, int NC>
-__device__ __forceinline__ void accum_two_rows(const float2* ex01, const float2* ex23,
-                                               const float* ey0, const float* ey1, int nc,
-                                               float2& a01, float2& a23, float2& b01, float2& b23) {
-  const float4* e0p = reinterpret_cast<const float4*>(ey0);
-  const float4* e1p = reinterpret_cast<const float4*>(ey1);
-#pragma unroll
-  for (int i = 0; i < NMAX; i += 4) {
-    if (NC == 0 && i >= nc) break;
-    const float4 e = e0p[i >> 2];
-    const float4 f = e1p[i >> 2];
-    a01 = ffma2(ex01[i + 0], e.x, a01);
-    a23 = ffma2(ex23[i + 0], e.x, a23);
-    b01 = ffma2(ex01[i + 0], f.x, b01);
-    b23 = ffma2(ex23[i + 0], f.x, b23);
-    a01 = ffma2(ex01[i + 1], e.y, a01);
-    a23 = ffma2(ex23[i + 1], e.y, a23);
-    b01 = ffma2(ex01[i + 1], f.y, b01);
-    b23 = ffma2(ex23[i + 1], f.y, b23);
-    a01 = ffma2(ex01[i + 2], e.z, a01);
-    a23 = ffma2(ex23[i + 2], e.z, a23);
-    b01 = ffma2(ex01[i + 2], f.z, b01);
-    b23 = ffma2(ex23[i + 2], f.z, b23);
-    a01 = ffma2(ex01[i + 3], e.w, a01);
-    a23 = ffma2(ex23[i + 3], e.w, a23);
-    b01 = ffma2(ex01[i + 3], f.w, b01);
-    b23 = ffma2(ex23[i + 3], f.w, b23);
-  }
-}
-
-}  // namespace
-
-template <int NMAX, typename TIn, typename TOut>
-__global__ void __launch_bounds__(kMapThreads, NMAX <= 16 ? 2 : 1)
-    map_stream_kernel(MapParams p, int band_h) {
+// Streaming kernel for frames whose rows allow CPT-pixel vector access (the
+// common case): persistent CTAs of 8 warps walk the frames' units (band of
+// up to 256 rows x group of 8 strips) in frame order; map_unit does the work.
+template <int NMAX, int CPT, typename TIn, typename TOut>
+__global__ void __launch_bounds__(kMapThreads, 2) map_stream_kernel(MapParams p, int band_h) {
   extern __shared__ float4 smem4[];
-  float* Ey = reinterpret_cast<float*>(smem4);                            // [band_h][NMAX]
-  uint4* ring = reinterpret_cast<uint4*>(Ey + (size_t)band_h * NMAX);     // [8][kStages][32]
-  __shared__ PointsSmem<NMAX> P;
+  float* Ey = reinterpret_cast<float*>(smem4);                          // [band_h][NMAX]
+  uint4* ring = reinterpret_cast<uint4*>(Ey + (size_t)band_h * NMAX);   // [8][kStages][32]
+  __shared__ PointsSmem<kMaxPts> P;
   __shared__ int s_kept;
-
-  constexpr int kInBytes = 4 * (int)sizeof(TIn);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int groups_x = (p.tiles_x + 7) / 8;
+  constexpr int kGroupW = kGroupStrips * 32 * CPT;
+  const int groups_x = (p.width + kGroupW - 1) / kGroupW;
   const int bands = (p.height + band_h - 1) / band_h;
   const long long units = (long long)p.n_frames * bands * groups_x;
   const size_t plane = (size_t)p.width * (size_t)p.height;
-  const bool has_depth = p.depth != nullptr;
-  uint4* my_ring = ring + (size_t)warp * kStages * 32;
-
+  uint4* my_ring = ring + (size_t)(threadIdx.x >> 5) * kStages * 32;
   for (long long u = blockIdx.x; u < units; u += gridDim.x) {
     const int f = (int)(u / ((long long)bands * groups_x));
     const int rem = (int)(u - (long long)f * bands * groups_x);
     const int b = rem / groups_x, g = rem - b * groups_x;
-    FrameRec* rec = const_cast<FrameRec*>(p.recs) + ((p.f0 + f) & p.rec_mask);
-    const int y0 = b * band_h;
-    const int rows = min(band_h, p.height - y0);
-    const int gx0 = g * 8 * kTileW;
-    const int gx1 = min(p.width, gx0 + 8 * kTileW) - 1;
-    const int x0 = gx0 + warp * kTileW;
-    const int xc = x0 + lane * 4;
-    const bool col_ok = xc < p.width;
-    const size_t row0 = (size_t)f * plane + (size_t)y0 * p.width + xc;
-    const char* dsrc = has_depth ? static_cast<const char*>(p.depth) + row0 * sizeof(TIn) : nullptr;
-    const size_t dstride = (size_t)p.width * sizeof(TIn);
-    auto issue = [&](int r) {
-      if (r < rows && col_ok && has_depth)
-        cp_async<kInBytes>(my_ring + (r % kStages) * 32 + lane, dsrc + (size_t)r * dstride);
-      cp_async_commit();
-    };
-    // The first depth rows are requested before the unit's set-up, so the
-    // copies are in flight while the factors are computed.  Each warp's ring
-    // is its own; the previous unit drained it.
-#pragma unroll
-    for (int s = 0; s < kStages - 2; ++s) issue(s);
-    __syncthreads();  // the previous unit is done with P and Ey
-    const int n = rec->n_valid;
-    const float inv_n = rec->inv_n;
-    if (warp == 0) {
-      bool keep = false;
-      float uh = 0.f, ul = 0.f, vh = 0.f, vl = 0.f, ch = 0.f, cl = 0.f;
-      if (lane < n) {
-        uh = rec->ux_hi[lane];
-        ul = rec->ux_lo[lane];
-        vh = rec->vy_hi[lane];
-        vl = rec->vy_lo[lane];
-        ch = rec->c_hi[lane];
-        cl = rec->c_lo[lane];
-        // the factors peak at the unit's pixel nearest (u, v)
-        const float xn = fminf(fmaxf(rintf(uh + ul), (float)gx0), (float)gx1);
-        const float yn = fminf(fmaxf(rintf(vh + vl), (float)y0), (float)(y0 + rows - 1));
-        const float peak = gauss_factor(xn, uh, ul, ch, cl) * gauss_factor(yn, vh, vl, ch, cl);
-        keep = peak * inv_n >= kCullBelow;
-      }
-      const unsigned mask = __ballot_sync(0xffffffffu, keep);
-      if (keep) {
-        const int pos = __popc(mask & ((1u << lane) - 1u));
-        P.uhi[pos] = uh;
-        P.ulo[pos] = ul;
-        P.vhi[pos] = vh;
-        P.vlo[pos] = vl;
-        P.chi[pos] = ch;
-        P.clo[pos] = cl;
-      }
-      if (lane == 0) s_kept = __popc(mask);
-    }
-    __syncthreads();
-    const int nk = s_kept;
-    const int nc = min(NMAX, (nk + 3) & ~3);
-    for (int r = warp; r < rows; r += kMapThreads / 32)
-      for (int i = lane; i < nc; i += 32)
-        Ey[r * NMAX + i] =
-            i < nk ? gauss_factor((float)(y0 + r), P.vhi[i], P.vlo[i], P.chi[i], P.clo[i]) * inv_n
-                   : 0.0f;
-    float2 ex01[NMAX], ex23[NMAX];
-#pragma unroll
-    for (int i = 0; i < NMAX; ++i) {
-      if (i < nc) {
-        float e0 = 0.f, e1 = 0.f, e2 = 0.f, e3 = 0.f;
-        if (i < nk && col_ok) {
-          e0 = gauss_factor((float)(xc + 0), P.uhi[i], P.ulo[i], P.chi[i], P.clo[i]);
-          e1 = gauss_factor((float)(xc + 1), P.uhi[i], P.ulo[i], P.chi[i], P.clo[i]);
-          e2 = gauss_factor((float)(xc + 2), P.uhi[i], P.ulo[i], P.chi[i], P.clo[i]);
-          e3 = gauss_factor((float)(xc + 3), P.uhi[i], P.ulo[i], P.chi[i], P.clo[i]);
-        }
-        ex01[i] = make_float2(e0, e1);
-        ex23[i] = make_float2(e2, e3);
-      }
-    }
-    __syncthreads();  // Ey complete
-    if (x0 >= p.width) continue;  // warp-uniform: this strip lies past the frame
-    float best = -1.0f;
-    unsigned bidx = 0;
-    auto emit = [&](const float2& a01, const float2& a23, const float4& dv, int r) {
-      const float4 m = make_float4(a01.x, a01.y, a23.x, a23.y);
-      const size_t idx = row0 + (size_t)r * p.width;
-      if (p.M) Px<TOut>::store4(p.M, idx, m);
-      if (p.G) {
-        float4 gv;
-        gv.x = m.x * depth_weight(dv.x, p.d0);
-        gv.y = m.y * depth_weight(dv.y, p.d0);
-        gv.z = m.z * depth_weight(dv.z, p.d0);
-        gv.w = m.w * depth_weight(dv.w, p.d0);
-        Px<TOut>::store4(p.G, idx, gv);
-      }
-      const float m4 = fmaxf(fmaxf(m.x, m.y), fmaxf(m.z, m.w));
-      if (m4 > best) {
-        best = m4;
-        const unsigned pix = (unsigned)((y0 + r) * p.width + xc);
-        bidx = m.x == m4 ? pix : (m.y == m4 ? pix + 1 : (m.z == m4 ? pix + 2 : pix + 3));
-      }
-    };
-    // Rows r and r+1 per iteration: the ring slots of rows r-2 and r-1 were
-    // consumed by the previous iteration, so rows r+kStages-2 and
-    // r+kStages-1 can be requested before rows r, r+1 are read.
-    for (int r = 0; r < rows; r += 2) {
-      issue(r + kStages - 2);
-      issue(r + kStages - 1);
-      cp_async_wait<kStages - 2>();
-      const bool two = r + 1 < rows;
-      float4 d0v = make_float4(0.f, 0.f, 0.f, 0.f), d1v = d0v;
-      if (has_depth) {
-        d0v = unpack4<TIn>(my_ring[(r % kStages) * 32 + lane]);
-        if (two) d1v = unpack4<TIn>(my_ring[((r + 1) % kStages) * 32 + lane]);
-      }
-      float2 a01 = make_float2(0.f, 0.f), a23 = a01, b01 = a01, b23 = a01;
-      const float* ey0 = Ey + r * NMAX;
-      const float* ey1 = Ey + (two ? r + 1 : r) * NMAX;
-      if (nc == NMAX)
-        accum_two_rows<NMAX, NMAX>(ex01, ex23, ey0, ey1, nc, a01, a23, b01, b23);
-      else
-        accum_two_rows<NMAX, 0>(ex01, ex23, ey0, ey1, nc, a01, a23, b01, b23);
-      if (!col_ok) continue;
-      emit(a01, a23, d0v, r);
-      if (two) emit(b01, b23, d1v, r + 1);
-    }
-    cp_async_wait<0>();
-    unsigned long long key =
-        best >= 0.0f ? ((unsigned long long)__float_as_uint(best) << 32) | (0xffffffffu - bidx) : 0ull;
-    for (int o = 16; o > 0; o >>= 1) {
-      const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
-      key = k2 > key ? k2 : key;
-    }
-    if (lane == 0 && n > 0 && key) atomicMax(&rec->argmax_key, key);
+    UnitGeom ug;
+    ug.rec = const_cast<FrameRec*>(p.recs) + ((p.f0 + f) & p.rec_mask);
+    ug.depth = p.depth ? static_cast<const char*>(p.depth) + (size_t)f * plane * sizeof(TIn) : nullptr;
+    ug.M = p.M ? static_cast<char*>(p.M) + (size_t)f * plane * sizeof(TOut) : nullptr;
+    ug.G = p.G ? static_cast<char*>(p.G) + (size_t)f * plane * sizeof(TOut) : nullptr;
+    ug.width = p.width;
+    ug.height = p.height;
+    ug.y0 = b * band_h;
+    ug.rows = min(band_h, p.height - ug.y0);
+    ug.gx0 = g * kGroupW;
+    ug.d0 = p.d0;
+    map_unit<NMAX, CPT, TIn, TOut>(ug, Ey, my_ring, P, s_kept);
   }
 }
 
@@ -550,41 +290,43 @@ int map_tile_h(int width, int height, int window) {
 
 namespace {
 
+// Resident CTAs per SM and SM count for a kernel (cached per instantiation).
+template <typename K>
+void occupancy(K k, size_t smem_max, int* per_sm, int* sms) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k, kMapThreads, smem_max);
+  if (*per_sm < 1) *per_sm = 1;
+}
+
 template <int NMAX, typename TIn, typename TOut>
 cudaError_t launch_typed(const MapParams& p, cudaStream_t st) {
-  const size_t smem = (size_t)NMAX * kTileW * 4 + (size_t)p.tile_h * NMAX * 4;
-  const long long blocks = (long long)p.n_frames * p.tiles_x * p.tiles_y;
-  if (blocks <= 0) return cudaSuccess;
-  if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  auto aligned = [](const void* q, int a) { return q == nullptr || ((uintptr_t)q % a) == 0; };
-  const bool vec = (p.width % 4) == 0 && aligned(p.depth, Px<TIn>::kAlign) &&
-                   aligned(p.M, Px<TOut>::kAlign) && aligned(p.G, Px<TOut>::kAlign);
+  const long long tiles = (long long)p.n_frames * p.tiles_x * p.tiles_y;
+  if (tiles <= 0) return cudaSuccess;
+  if (tiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  // windows up to 16 points: 4 columns per lane; 32 points: 2 (register budget)
+  constexpr int CPT = NMAX <= 16 ? 4 : 2;
+  auto aligned = [](const void* q, size_t a) { return q == nullptr || ((uintptr_t)q % a) == 0; };
+  const bool vec = (p.width % CPT) == 0 && aligned(p.depth, CPT * sizeof(TIn)) &&
+                   aligned(p.M, CPT * sizeof(TOut)) && aligned(p.G, CPT * sizeof(TOut));
   if (vec) {
-    // streaming kernel: persistent grid of (SMs x resident CTAs)
     const int bands = (p.height + kBandMax - 1) / kBandMax;
     const int band_h = (p.height + bands - 1) / bands;
-    const size_t smem2 = (size_t)band_h * NMAX * 4 + (size_t)(kMapThreads / 32) * kStages * 32 * 16;
-    auto k = map_stream_kernel<NMAX, TIn, TOut>;
+    auto k = map_stream_kernel<NMAX, CPT, TIn, TOut>;
     static int per_sm = -1, sms = 0;
-    if (per_sm < 0) {
-      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(kBandMax * NMAX * 4 + (kMapThreads / 32) * kStages * 32 * 16));
-      int dev = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kMapThreads,
-                                                    (size_t)kBandMax * NMAX * 4 +
-                                                        (kMapThreads / 32) * kStages * 32 * 16);
-      if (per_sm < 1) per_sm = 1;
-    }
-    const long long units = (long long)p.n_frames * ((p.height + band_h - 1) / band_h) *
-                            ((p.tiles_x + 7) / 8);
+    if (per_sm < 0) occupancy(k, unit_smem_bytes(NMAX, kBandMax), &per_sm, &sms);
+    constexpr int kGroupW = kGroupStrips * 32 * CPT;
+    const long long units =
+        (long long)p.n_frames * bands * ((p.width + kGroupW - 1) / kGroupW);
     const long long grid = std::min<long long>(units, (long long)sms * per_sm);
-    k<<<(unsigned)grid, kMapThreads, smem2, st>>>(p, band_h);
+    k<<<(unsigned)grid, kMapThreads, unit_smem_bytes(NMAX, band_h), st>>>(p, band_h);
   } else {
+    const size_t smem = (size_t)NMAX * kTileW * 4 + (size_t)p.tile_h * NMAX * 4;
     auto k = map_kernel<NMAX, TIn, TOut, false>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k<<<(unsigned)blocks, kMapThreads, smem, st>>>(p);
+    k<<<(unsigned)tiles, kMapThreads, smem, st>>>(p);
   }
   return cudaGetLastError();
 }

@@ -1,0 +1,367 @@
+// Device code shared by the per-stream and the batched map kernels: the
+// motion-focus map of Eq. 7 and the motion-guided depth over one "unit" (a
+// band of up to 256 rows of one frame, across a group of 8 adjacent strips of
+// 32*CPT columns), with the frame's argmax.  Both launch paths run exactly
+// this code, so a frame's maps do not depend on which path, batch or tile
+// schedule produced them.
+//
+// Per unit:
+//   * warp 0 keeps only the points whose Gaussian can reach the unit: a point
+//     whose largest column factor over the unit times its largest row factor
+//     (times 1/Z) is below 2^-40 contributes less than 2^-40 to every pixel
+//     of it, far inside the 1e-10 absolute floor of the map tolerance; kept
+//     points keep their order;
+//   * the CTA evaluates the band's row factors once in shared memory;
+//   * each warp owns one strip: every lane holds its CPT columns' factors for
+//     the kept points in registers and streams the band's rows two at a time
+//     (CPT/2 x 2 independent FMA chains), depth arriving through the warp's
+//     ring of kStages cp.async stages, maps leaving through streaming stores.
+// The map is a sum of N isotropic Gaussians, so each term factors as
+//     exp(-((x-u)^2 + (y-v)^2) c) = exp(-(x-u)^2 c) * exp(-(y-v)^2 c),
+// c = 1/(2 sigma_i^2); every pixel then costs one FP32 FMA per kept point,
+// issued two pixels at a time (fma.rn.f32x2), in point order.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <math.h>
+
+#include "mf_internal.h"
+
+namespace mf {
+
+constexpr int kStages = 6;       // depth rows in flight per warp
+constexpr int kBandMax = 256;    // rows per unit
+constexpr int kGroupStrips = 8;  // strips (one per warp) per unit
+constexpr float kCullBelow = 9.094947017729282e-13f;  // 2^-40
+
+template <int NMAX>
+struct PointsSmem {
+  float uhi[NMAX], ulo[NMAX], vhi[NMAX], vlo[NMAX], chi[NMAX], clo[NMAX];
+};
+
+// exp(-(q - hi - lo)^2 * (chi + clo)) for an integer-valued q.  hi lies on a
+// 2^-8 grid with |hi| < 2^15, so q - hi is exact; the square is carried as a
+// compensated pair and 1/(2 sigma^2) as a float pair, which keeps the
+// exponent's relative error near one FP32 rounding before expf (<= 2 ulp).
+__device__ __forceinline__ float gauss_factor(float q, float hi, float lo, float chi, float clo) {
+  const float dh = q - hi;
+  const float p2 = dh * dh;
+  const float e2 = fmaf(dh, dh, -p2);   // dh^2 = p2 + e2 exactly
+  float qq = fmaf(-2.0f * dh, lo, e2);  // (dh - lo)^2 = p2 + qq
+  qq = fmaf(lo, lo, qq);
+  const float t1 = fmaf(clo, p2, chi * qq);
+  const float a = fmaf(chi, p2, t1);
+  return expf(-a);
+}
+
+__device__ __forceinline__ float2 ffma2(float2 a, float b, float2 c) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\t"
+      "mov.b64 rb, {%4, %4};\n\t"
+      "mov.b64 rc, {%5, %6};\n\t"
+      "fma.rn.f32x2 rd, ra, rb, rc;\n\t"
+      "mov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b), "f"(c.x), "f"(c.y));
+  return d;
+}
+
+// min(1, d0 / D) for finite D > 0, else 0 (NaN fails both comparisons).
+__device__ __forceinline__ float depth_weight(float D, float d0) {
+  return (D > 0.0f && D <= 3.402823466e38f) ? fminf(1.0f, __fdividef(d0, D)) : 0.0f;
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* dst, const void* src) {
+  if (BYTES == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src));
+  else if (BYTES == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(dst)), "l"(src));
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(dst)), "l"(src));
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+// CPT consecutive storage elements <-> floats.
+template <typename T, int CPT>
+struct Vec;
+
+template <int CPT>
+struct Vec<float, CPT> {
+  static __device__ __forceinline__ void unpack(const uint4& r, float (&d)[CPT]) {
+    d[0] = __uint_as_float(r.x);
+    d[1] = __uint_as_float(r.y);
+    if (CPT == 4) {
+      d[CPT > 2 ? 2 : 0] = __uint_as_float(r.z);
+      d[CPT > 3 ? 3 : 0] = __uint_as_float(r.w);
+    }
+  }
+  static __device__ __forceinline__ void store(void* plane, size_t i, const float (&v)[CPT]) {
+    float* q = static_cast<float*>(plane) + i;
+    if (CPT == 4)
+      __stcs(reinterpret_cast<float4*>(q), make_float4(v[0], v[1], v[CPT > 2 ? 2 : 0], v[CPT > 3 ? 3 : 0]));
+    else
+      __stcs(reinterpret_cast<float2*>(q), make_float2(v[0], v[1]));
+  }
+};
+
+template <typename H>
+struct Half2Of;
+template <>
+struct Half2Of<__nv_bfloat16> {
+  static __device__ __forceinline__ float2 to_f2(unsigned w) {
+    return __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&w));
+  }
+  static __device__ __forceinline__ unsigned from_f2(float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<unsigned*>(&h);
+  }
+};
+template <>
+struct Half2Of<__half> {
+  static __device__ __forceinline__ float2 to_f2(unsigned w) {
+    return __half22float2(*reinterpret_cast<__half2*>(&w));
+  }
+  static __device__ __forceinline__ unsigned from_f2(float a, float b) {
+    __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<unsigned*>(&h);
+  }
+};
+
+template <typename H, int CPT>
+struct Vec16 {
+  static __device__ __forceinline__ void unpack(const uint4& r, float (&d)[CPT]) {
+    const float2 a = Half2Of<H>::to_f2(r.x);
+    d[0] = a.x;
+    d[1] = a.y;
+    if (CPT == 4) {
+      const float2 c = Half2Of<H>::to_f2(r.y);
+      d[CPT > 2 ? 2 : 0] = c.x;
+      d[CPT > 3 ? 3 : 0] = c.y;
+    }
+  }
+  static __device__ __forceinline__ void store(void* plane, size_t i, const float (&v)[CPT]) {
+    H* q = static_cast<H*>(plane) + i;
+    if (CPT == 4) {
+      uint2 w;
+      w.x = Half2Of<H>::from_f2(v[0], v[1]);
+      w.y = Half2Of<H>::from_f2(v[CPT > 2 ? 2 : 0], v[CPT > 3 ? 3 : 0]);
+      __stcs(reinterpret_cast<uint2*>(q), w);
+    } else {
+      __stcs(reinterpret_cast<unsigned*>(q), Half2Of<H>::from_f2(v[0], v[1]));
+    }
+  }
+};
+template <int CPT>
+struct Vec<__nv_bfloat16, CPT> : Vec16<__nv_bfloat16, CPT> {};
+template <int CPT>
+struct Vec<__half, CPT> : Vec16<__half, CPT> {};
+
+// Two rows' sums for one lane's CPT columns, points 0..nc-1 in order.  NC > 0
+// fixes the trip count at compile time (all NMAX points kept).
+template <int NMAX, int CPT, int NC>
+__device__ __forceinline__ void accum_two_rows(const float2 (&ex)[NMAX][CPT / 2], const float* ey0,
+                                               const float* ey1, int nc, float2 (&a)[CPT / 2],
+                                               float2 (&b)[CPT / 2]) {
+  const float4* e0p = reinterpret_cast<const float4*>(ey0);
+  const float4* e1p = reinterpret_cast<const float4*>(ey1);
+#pragma unroll
+  for (int i = 0; i < NMAX; i += 4) {
+    if (NC == 0 && i >= nc) break;
+    const float4 e = e0p[i >> 2];
+    const float4 f = e1p[i >> 2];
+    const float es[4] = {e.x, e.y, e.z, e.w};
+    const float fs[4] = {f.x, f.y, f.z, f.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+#pragma unroll
+      for (int c = 0; c < CPT / 2; ++c) {
+        a[c] = ffma2(ex[i + k][c], es[k], a[c]);
+        b[c] = ffma2(ex[i + k][c], fs[k], b[c]);
+      }
+    }
+  }
+}
+
+// One unit of one frame.  planes point at the frame's first pixel; the
+// caller guarantees width % CPT == 0 and CPT-element alignment of all
+// planes.  Every thread of the CTA must call this (it holds barriers).
+struct UnitGeom {
+  FrameRec* rec;
+  const char* depth;  // frame plane or NULL
+  char* M;            // frame plane or NULL
+  char* G;            // frame plane or NULL
+  int width, height;
+  int y0, rows;       // band
+  int gx0;            // first column of the strip group
+  float d0;
+};
+
+template <int NMAX, int CPT, typename TIn, typename TOut>
+__device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* my_ring,
+                                         PointsSmem<kMaxPts>& P, int& s_kept) {
+  constexpr int kInBytes = CPT * (int)sizeof(TIn);
+  constexpr int kStrip = 32 * CPT;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int rows = ug.rows, y0 = ug.y0;
+  const int x0 = ug.gx0 + warp * kStrip;
+  const int xc = x0 + lane * CPT;
+  const bool col_ok = xc < ug.width;
+  const int gx1 = min(ug.width, ug.gx0 + kGroupStrips * kStrip) - 1;
+  const size_t row0 = (size_t)y0 * ug.width + xc;
+  const char* dsrc = ug.depth ? ug.depth + row0 * sizeof(TIn) : nullptr;
+  const size_t dstride = (size_t)ug.width * sizeof(TIn);
+  auto issue = [&](int r) {
+    if (r < rows && col_ok && dsrc)
+      cp_async<kInBytes>(my_ring + (r % kStages) * 32 + lane, dsrc + (size_t)r * dstride);
+    cp_async_commit();
+  };
+  // The first depth rows are requested before the set-up, so the copies are
+  // in flight while the factors are computed.  The ring is this warp's own
+  // and the previous unit drained it.
+#pragma unroll
+  for (int s = 0; s < kStages - 2; ++s) issue(s);
+  __syncthreads();  // the previous unit is done with P and Ey
+
+  FrameRec* rec = ug.rec;
+  const int n = rec->n_valid;
+  const float inv_n = rec->inv_n;
+  if (warp == 0) {
+    bool keep = false;
+    float uh = 0.f, ul = 0.f, vh = 0.f, vl = 0.f, ch = 0.f, cl = 0.f;
+    if (lane < n) {
+      uh = rec->ux_hi[lane];
+      ul = rec->ux_lo[lane];
+      vh = rec->vy_hi[lane];
+      vl = rec->vy_lo[lane];
+      ch = rec->c_hi[lane];
+      cl = rec->c_lo[lane];
+      // the factors peak at the unit's pixel nearest (u, v)
+      const float xn = fminf(fmaxf(rintf(uh + ul), (float)ug.gx0), (float)gx1);
+      const float yn = fminf(fmaxf(rintf(vh + vl), (float)y0), (float)(y0 + rows - 1));
+      const float peak = gauss_factor(xn, uh, ul, ch, cl) * gauss_factor(yn, vh, vl, ch, cl);
+      keep = peak * inv_n >= kCullBelow;
+    }
+    const unsigned mask = __ballot_sync(0xffffffffu, keep);
+    if (keep) {
+      const int pos = __popc(mask & ((1u << lane) - 1u));
+      P.uhi[pos] = uh;
+      P.ulo[pos] = ul;
+      P.vhi[pos] = vh;
+      P.vlo[pos] = vl;
+      P.chi[pos] = ch;
+      P.clo[pos] = cl;
+    }
+    if (lane == 0) s_kept = __popc(mask);
+  }
+  __syncthreads();
+  const int nk = s_kept;  // <= NMAX: n never exceeds the window's bucket
+  const int nc = min(NMAX, (nk + 3) & ~3);
+  for (int r = warp; r < rows; r += kMapThreads / 32)
+    for (int i = lane; i < nc; i += 32)
+      Ey[r * NMAX + i] =
+          i < nk ? gauss_factor((float)(y0 + r), P.vhi[i], P.vlo[i], P.chi[i], P.clo[i]) * inv_n
+                 : 0.0f;
+  float2 ex[NMAX][CPT / 2];
+#pragma unroll
+  for (int i = 0; i < NMAX; ++i) {
+    if (i < nc) {
+#pragma unroll
+      for (int c = 0; c < CPT / 2; ++c) {
+        float e0 = 0.f, e1 = 0.f;
+        if (i < nk && col_ok) {
+          e0 = gauss_factor((float)(xc + 2 * c), P.uhi[i], P.ulo[i], P.chi[i], P.clo[i]);
+          e1 = gauss_factor((float)(xc + 2 * c + 1), P.uhi[i], P.ulo[i], P.chi[i], P.clo[i]);
+        }
+        ex[i][c] = make_float2(e0, e1);
+      }
+    }
+  }
+  __syncthreads();  // Ey complete
+  if (x0 >= ug.width) return;  // warp-uniform: this strip lies past the frame (no copies issued)
+
+  float best = -1.0f;
+  unsigned bidx = 0;
+  auto emit = [&](const float2 (&acc)[CPT / 2], const float (&dv)[CPT], int r) {
+    float m[CPT];
+#pragma unroll
+    for (int c = 0; c < CPT / 2; ++c) {
+      m[2 * c] = acc[c].x;
+      m[2 * c + 1] = acc[c].y;
+    }
+    const size_t idx = row0 + (size_t)r * ug.width;
+    if (ug.M) Vec<TOut, CPT>::store(ug.M, idx, m);
+    if (ug.G) {
+      float gv[CPT];
+#pragma unroll
+      for (int c = 0; c < CPT; ++c) gv[c] = m[c] * depth_weight(dv[c], ug.d0);
+      Vec<TOut, CPT>::store(ug.G, idx, gv);
+    }
+    float mm = m[0];
+#pragma unroll
+    for (int c = 1; c < CPT; ++c) mm = fmaxf(mm, m[c]);
+    if (mm > best) {
+      best = mm;
+      unsigned off = CPT - 1;
+#pragma unroll
+      for (int c = CPT - 2; c >= 0; --c)
+        if (m[c] == mm) off = c;
+      bidx = (unsigned)((y0 + r) * ug.width + xc) + off;
+    }
+  };
+  // Rows r and r+1 per iteration: the ring slots of rows r-2 and r-1 were
+  // consumed by the previous iteration, so rows r+kStages-2 and r+kStages-1
+  // can be requested before rows r, r+1 are read.
+  for (int r = 0; r < rows; r += 2) {
+    issue(r + kStages - 2);
+    issue(r + kStages - 1);
+    cp_async_wait<kStages - 2>();
+    const bool two = r + 1 < rows;
+    float d0v[CPT], d1v[CPT];
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) d0v[c] = d1v[c] = 0.0f;
+    if (dsrc) {
+      Vec<TIn, CPT>::unpack(my_ring[(r % kStages) * 32 + lane], d0v);
+      if (two) Vec<TIn, CPT>::unpack(my_ring[((r + 1) % kStages) * 32 + lane], d1v);
+    }
+    float2 a[CPT / 2], b[CPT / 2];
+#pragma unroll
+    for (int c = 0; c < CPT / 2; ++c) a[c] = b[c] = make_float2(0.f, 0.f);
+    const float* ey0 = Ey + r * NMAX;
+    const float* ey1 = Ey + (two ? r + 1 : r) * NMAX;
+    if (nc == NMAX)
+      accum_two_rows<NMAX, CPT, NMAX>(ex, ey0, ey1, nc, a, b);
+    else
+      accum_two_rows<NMAX, CPT, 0>(ex, ey0, ey1, nc, a, b);
+    if (!col_ok) continue;
+    emit(a, d0v, r);
+    if (two) emit(b, d1v, r + 1);
+  }
+  cp_async_wait<0>();
+  unsigned long long key =
+      best >= 0.0f ? ((unsigned long long)__float_as_uint(best) << 32) | (0xffffffffu - bidx) : 0ull;
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
+    key = k2 > key ? k2 : key;
+  }
+  if (lane == 0 && n > 0 && key) atomicMax(&rec->argmax_key, key);
+}
+
+// Dynamic shared memory of a CTA running units of bucket NMAX.
+__host__ __device__ constexpr size_t unit_smem_bytes(int nmax, int band_h) {
+  return (size_t)band_h * nmax * 4 + (size_t)(kMapThreads / 32) * kStages * 32 * 16;
+}
+
+}  // namespace mf
