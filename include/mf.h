@@ -254,6 +254,106 @@ int64_t mf_total_kernel_launches(void);
 const char* mf_last_error(void);
 
 /* ---------------------------------------------------------------------------
+ * Batched engine: many streams on one GPU, one batched launch per tick.
+ *
+ * The engine is the serving form of the same per-frame method (Sections
+ * 2.2-2.3): each admitted stream keeps its pose history resident on the
+ * GPU; frames submitted by any number of streams between two ticks are
+ * processed by ONE batch -- a CUDA graph of one table upload and four kernels
+ * (ingest + anchoring, motion points, the persistent map kernel over every
+ * frame's tiles whatever its resolution and window, result records).  Ticks
+ * are asynchronous and may overlap host-side preparation of the next one.
+ * A frame's maps are identical whether its stream runs alone or among
+ * others.  Tile heights are picked per resolution class by a built-in
+ * autotuner (mf_engine_tune) unless MF_ENGINE_NO_TUNE is set.
+ */
+typedef struct mf_engine mf_engine;
+
+#define MF_ENGINE_NO_GRAPH 2u /* launch the tick's kernels directly (no CUDA graph) */
+#define MF_ENGINE_NO_TUNE 4u  /* use the plain path's tile height, never tune */
+
+typedef struct {
+  int32_t max_streams;       /* stream slots (default 256) */
+  int32_t max_tick_frames;   /* emitted frames per tick over all streams (default 4096) */
+  int32_t max_stream_frames; /* frames one stream may emit per tick (default 64) */
+  int32_t depth_dtype;       /* storage type of all depth planes (mf_dtype) */
+  int32_t map_dtype;         /* storage type of all output maps (mf_dtype) */
+  uint32_t flags;            /* MF_ENGINE_* and MF_FLAG_TIME_KERNELS */
+  int64_t memory_budget;     /* device bytes admitted streams may account for; 0 = no limit */
+  void* cuda_stream;         /* as in mf_stream_desc */
+} mf_engine_desc;
+
+typedef struct {
+  int64_t ticks;             /* ticks launched */
+  int64_t frames;            /* frames processed */
+  int64_t units;             /* map tiles processed */
+  int64_t kernel_launches;   /* kernels run by the ticks (graph nodes included) */
+  int64_t graph_launches;    /* CUDA graph launches */
+  int32_t streams;           /* admitted streams */
+  int32_t reserved;
+  int64_t device_bytes;      /* device memory held by the engine */
+  int64_t accounted_bytes;   /* engine memory + admitted streams' reservations */
+  double tick_gpu_ms;        /* with MF_FLAG_TIME_KERNELS: summed GPU time of the ticks */
+} mf_engine_stats;
+
+/* Defaults: 256 streams, 4096 frames per tick, 64 per stream, FP32, no
+ * budget, library-owned stream. */
+void mf_engine_desc_init(mf_engine_desc* d);
+
+/* Allocate the engine's tick tables (pinned + device, double-buffered), the
+ * per-tick frame records and the stream slots.  MF_ERR_INVALID_ARG, MF_ERR_OOM. */
+int mf_engine_open(const mf_engine_desc* d, mf_engine** out);
+
+/* Admit a stream described by *d (its dtypes must equal the engine's, its
+ * width must be even; its cuda_stream and allocator fields are ignored).  The stream's pose history
+ * is allocated on the device and stays resident until removal.
+ * reserve_bytes: device memory the caller will hold for this stream (its
+ * output planes, say), counted with the history against memory_budget.
+ * On success *slot names the stream.  MF_ERR_ADMISSION when every slot is
+ * taken or the budget would be exceeded; MF_ERR_INVALID_ARG for a bad
+ * descriptor.  May run the autotuner for a new resolution class. */
+int mf_engine_add_stream(mf_engine* e, const mf_stream_desc* d, int64_t reserve_bytes,
+                         int32_t* slot);
+
+/* Free a slot (waits for the ticks that used it).  Its frames must not be
+ * pending (submitted after the last tick). */
+int mf_engine_remove_stream(mf_engine* e, int32_t slot);
+
+/* Queue one push of stream `slot` for the next tick (Section 2.2 semantics,
+ * as mf_push_frames): n poses (host memory, n x 12 FP64, copied now), n depth
+ * planes (device memory; planes of overlap frames are not read; NULL allowed),
+ * K (host, fx fy cx cy).  The emitted frames' maps go to focus_map /
+ * guided_depth (device planes, n_emit each, or NULL) and their records to
+ * info (device, n_emit records, or NULL).  Device buffers are read and
+ * written when the tick runs: keep them valid until it is done.
+ * MF_ERR_NOT_READY if the stream already has a push in this tick or the tick
+ * is full; MF_ERR_INVALID_ARG as mf_push_frames, or for planes not aligned
+ * to two elements. */
+int mf_engine_submit(mf_engine* e, int32_t slot, int32_t n, const double* poses_w2c_3x4,
+                     const void* depth, const double* K, void* focus_map, void* guided_depth,
+                     mf_frame_info* info);
+
+/* Launch everything submitted since the previous tick as one batch.  Does
+ * not wait.  *tick receives its id (-1 if nothing was submitted). */
+int mf_engine_tick(mf_engine* e, int64_t* tick);
+
+/* *done = 1 when tick `tick` (and every earlier one) has finished. */
+int mf_engine_query(mf_engine* e, int64_t tick, int32_t* done);
+
+/* Wait for tick `tick` (bounded by timeout_ns; < 0 = no bound). */
+int mf_engine_wait(mf_engine* e, int64_t tick, int64_t timeout_ns);
+
+/* Time the map kernel on a synthetic batch of width x height frames with a
+ * window of `window` points for each candidate tile height and keep the
+ * fastest for that resolution class; *band_h receives it.  Synchronous. */
+int mf_engine_tune(mf_engine* e, int32_t width, int32_t height, int32_t window, int32_t* band_h);
+
+int mf_engine_get_stats(mf_engine* e, mf_engine_stats* out);
+
+/* Wait for all ticks and free everything. */
+int mf_engine_close(mf_engine* e);
+
+/* ---------------------------------------------------------------------------
  * Allocation-free rendering.  The paper has no counterpart to this entry
  * point; it exists for callers that cannot let a library allocate device
  * memory: real-time loops that must never meet a cudaMalloc (it can

@@ -25,7 +25,12 @@ MF_FLAG_TIME_KERNELS = 1
 EXPORTED = ("mf_stream_desc_init", "mf_open_stream", "mf_push_frames", "mf_get_maps",
             "mf_sync", "mf_pending_frames", "mf_reset_stream", "mf_stream_stats",
             "mf_close_stream", "mf_status_string", "mf_version", "mf_total_kernel_launches",
-            "mf_last_error", "mf_render_noalloc")
+            "mf_last_error", "mf_render_noalloc", "mf_engine_desc_init", "mf_engine_open",
+            "mf_engine_add_stream", "mf_engine_remove_stream", "mf_engine_submit",
+            "mf_engine_tick", "mf_engine_query", "mf_engine_wait", "mf_engine_tune",
+            "mf_engine_get_stats", "mf_engine_close")
+MF_ENGINE_NO_GRAPH = 2
+MF_ENGINE_NO_TUNE = 4
 MF_NOALLOC_MAX_FRAMES = 256
 MF_NOALLOC_MAX_POSES = MF_NOALLOC_MAX_FRAMES + 63
 
@@ -55,6 +60,25 @@ class MFStats(ctypes.Structure):
         ("frames_rendered", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
         ("map_launches", ctypes.c_int64), ("map_kernel_ms", ctypes.c_double),
         ("device_bytes", ctypes.c_int64),
+    ]
+
+
+class MFEngineDesc(ctypes.Structure):
+    _fields_ = [
+        ("max_streams", ctypes.c_int32), ("max_tick_frames", ctypes.c_int32),
+        ("max_stream_frames", ctypes.c_int32), ("depth_dtype", ctypes.c_int32),
+        ("map_dtype", ctypes.c_int32), ("flags", ctypes.c_uint32),
+        ("memory_budget", ctypes.c_int64), ("cuda_stream", ctypes.c_void_p),
+    ]
+
+
+class MFEngineStats(ctypes.Structure):
+    _fields_ = [
+        ("ticks", ctypes.c_int64), ("frames", ctypes.c_int64), ("units", ctypes.c_int64),
+        ("kernel_launches", ctypes.c_int64), ("graph_launches", ctypes.c_int64),
+        ("streams", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("device_bytes", ctypes.c_int64), ("accounted_bytes", ctypes.c_int64),
+        ("tick_gpu_ms", ctypes.c_double),
     ]
 
 
@@ -102,9 +126,25 @@ def _load():
     lib.mf_last_error.restype = ctypes.c_char_p
     lib.mf_render_noalloc.argtypes = [ctypes.POINTER(MFStreamDesc), i32, vp, i32, vp, vp, vp, vp,
                                       vp]
+    lib.mf_engine_desc_init.argtypes = [ctypes.POINTER(MFEngineDesc)]
+    lib.mf_engine_desc_init.restype = None
+    lib.mf_engine_open.argtypes = [ctypes.POINTER(MFEngineDesc), ctypes.POINTER(vp)]
+    lib.mf_engine_add_stream.argtypes = [vp, ctypes.POINTER(MFStreamDesc), i64,
+                                         ctypes.POINTER(i32)]
+    lib.mf_engine_remove_stream.argtypes = [vp, i32]
+    lib.mf_engine_submit.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp]
+    lib.mf_engine_tick.argtypes = [vp, ctypes.POINTER(i64)]
+    lib.mf_engine_query.argtypes = [vp, i64, ctypes.POINTER(i32)]
+    lib.mf_engine_wait.argtypes = [vp, i64, i64]
+    lib.mf_engine_tune.argtypes = [vp, i32, i32, i32, ctypes.POINTER(i32)]
+    lib.mf_engine_get_stats.argtypes = [vp, ctypes.POINTER(MFEngineStats)]
+    lib.mf_engine_close.argtypes = [vp]
     for name in ("mf_open_stream", "mf_push_frames", "mf_get_maps", "mf_sync",
                  "mf_pending_frames", "mf_reset_stream", "mf_stream_stats", "mf_close_stream",
-                 "mf_render_noalloc"):
+                 "mf_render_noalloc", "mf_engine_open", "mf_engine_add_stream",
+                 "mf_engine_remove_stream", "mf_engine_submit", "mf_engine_tick",
+                 "mf_engine_query", "mf_engine_wait", "mf_engine_tune", "mf_engine_get_stats",
+                 "mf_engine_close"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -208,3 +248,69 @@ def mf_render_noalloc(desc, n_poses, poses, n_render, depth, K, focus_map=None,
     _check(lib.mf_render_noalloc(ctypes.byref(desc), int(n_poses), ptr(poses), int(n_render),
                                  ptr(depth), ptr(K), ptr(focus_map), ptr(guided_depth), ptr(info)),
            "mf_render_noalloc")
+
+
+# ----------------------------------------------------------- engine --------
+def mf_engine_desc_init(**fields):
+    d = MFEngineDesc()
+    lib.mf_engine_desc_init(ctypes.byref(d))
+    for k, v in fields.items():
+        if not hasattr(d, k):
+            raise TypeError(f"unknown engine field {k}")
+        setattr(d, k, v)
+    return d
+
+
+def mf_engine_open(desc):
+    h = ctypes.c_void_p()
+    _check(lib.mf_engine_open(ctypes.byref(desc), ctypes.byref(h)), "mf_engine_open")
+    return h.value
+
+
+def mf_engine_add_stream(e, stream_desc, reserve_bytes=0):
+    slot = ctypes.c_int32()
+    _check(lib.mf_engine_add_stream(e, ctypes.byref(stream_desc), int(reserve_bytes),
+                                    ctypes.byref(slot)), "mf_engine_add_stream")
+    return slot.value
+
+
+def mf_engine_remove_stream(e, slot):
+    _check(lib.mf_engine_remove_stream(e, int(slot)), "mf_engine_remove_stream")
+
+
+def mf_engine_submit(e, slot, n, poses, depth, K, focus_map=None, guided_depth=None, info=None):
+    _check(lib.mf_engine_submit(e, int(slot), int(n), ptr(poses), ptr(depth), ptr(K),
+                                ptr(focus_map), ptr(guided_depth), ptr(info)), "mf_engine_submit")
+
+
+def mf_engine_tick(e):
+    t = ctypes.c_int64()
+    _check(lib.mf_engine_tick(e, ctypes.byref(t)), "mf_engine_tick")
+    return t.value
+
+
+def mf_engine_query(e, tick):
+    d = ctypes.c_int32()
+    _check(lib.mf_engine_query(e, int(tick), ctypes.byref(d)), "mf_engine_query")
+    return bool(d.value)
+
+
+def mf_engine_wait(e, tick, timeout_ns=-1):
+    _check(lib.mf_engine_wait(e, int(tick), int(timeout_ns)), "mf_engine_wait")
+
+
+def mf_engine_tune(e, width, height, window):
+    b = ctypes.c_int32()
+    _check(lib.mf_engine_tune(e, int(width), int(height), int(window), ctypes.byref(b)),
+           "mf_engine_tune")
+    return b.value
+
+
+def mf_engine_get_stats(e):
+    st = MFEngineStats()
+    _check(lib.mf_engine_get_stats(e, ctypes.byref(st)), "mf_engine_get_stats")
+    return st
+
+
+def mf_engine_close(e):
+    _check(lib.mf_engine_close(e), "mf_engine_close")

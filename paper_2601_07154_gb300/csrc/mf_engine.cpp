@@ -1,0 +1,742 @@
+// Batched engine (include/mf.h, "Batched engine"): stream slots with
+// resident pose histories, admission against a device-memory budget, ticks
+// that process every submitted push as one batch (a CUDA graph of the tick
+// table upload and four kernels), and the tile-height autotuner.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <new>
+#include <thread>
+#include <tuple>
+#include <vector>
+
+#include "mf_engine_internal.h"
+
+using mf::FrameRec;
+using mf::SlotParams;
+using mf::TickFrame;
+using mf::TickHeader;
+using mf::TickPush;
+
+namespace {
+
+size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+size_t dtype_bytes(int dt) { return dt == MF_F32 ? 4 : 2; }
+int64_t pow2_at_least(int64_t v) {
+  int64_t c = 1;
+  while (c < v) c <<= 1;
+  return c;
+}
+
+int fail(int st, const char* what, cudaError_t e = cudaSuccess) { return mf::host_fail(st, what, e); }
+
+#define ENG_CUDA(call, what)                                   \
+  do {                                                         \
+    cudaError_t e_ = (call);                                   \
+    if (e_ != cudaSuccess) return fail(MF_ERR_CUDA, what, e_); \
+  } while (0)
+
+bool on_device(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// Plain-path tile height (used without tuning).
+int default_band(int height) {
+  const int bands = (height + mf::kBandMax - 1) / mf::kBandMax;
+  return (height + bands - 1) / bands;
+}
+
+struct Slot {
+  bool used = false;
+  mf_stream_desc d{};
+  double* ring = nullptr;
+  int32_t* ring_bad = nullptr;
+  int64_t ring_cap = 0;
+  int64_t emitted = 0, pushes = 0;
+  int64_t reserve = 0;
+  int64_t pending_tick = -1;  // tick id of the slot's queued push
+  int64_t last_tick = -1;     // last tick that used the slot
+  size_t plane_in = 0, plane_out = 0;
+  int band_h = 0, bands = 0, groups_x = 0;
+};
+
+}  // namespace
+
+struct mf_engine {
+  mf_engine_desc d{};
+  int device = 0;
+  cudaStream_t st = nullptr, cap_st = nullptr;
+  bool own_stream = false;
+  std::vector<Slot> slots;
+  SlotParams* slots_dev = nullptr;  // max_streams + 1 entries (the last: tuner)
+  FrameRec* recs = nullptr;
+  size_t tab_bytes = 0;
+  char* host_tab[2] = {nullptr, nullptr};
+  char* dev_tab[2] = {nullptr, nullptr};
+  cudaGraph_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  cudaGraphNode_t copy_node[2] = {nullptr, nullptr};
+  cudaEvent_t done[2] = {nullptr, nullptr};
+  cudaEvent_t t0[2] = {nullptr, nullptr};
+  int64_t buf_tick[2] = {-1, -1};
+  int map_grid = 0;
+  // the tick being assembled
+  std::vector<TickPush> pushes;
+  std::vector<TickFrame> frames;
+  std::vector<double> poses;
+  int64_t next_tick = 0;
+  std::map<std::tuple<int, int, int>, int> tuned;  // (width, height, window) -> band_h
+  // statistics
+  int64_t ticks = 0, frames_done = 0, units_done = 0, launches = 0, graph_launches = 0;
+  int64_t device_bytes = 0;
+  double tick_ms = 0.0;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending_timers;
+
+  void* dalloc(size_t n) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, n) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    device_bytes += (int64_t)n;
+    return p;
+  }
+  void dfree(void* p, size_t n) {
+    if (!p) return;
+    cudaFree(p);
+    device_bytes -= (int64_t)n;
+  }
+  size_t poses_cap() const {
+    return (size_t)d.max_tick_frames + (size_t)d.max_streams * (MF_MAX_HISTORY - 1);
+  }
+  int64_t accounted() const {
+    int64_t a = device_bytes;
+    for (const Slot& s : slots)
+      if (s.used) a += s.reserve;
+    return a;
+  }
+};
+
+namespace {
+
+size_t table_bytes(size_t frames, size_t pushes, size_t poses) {
+  size_t off = align256(sizeof(TickHeader));
+  off = align256(off + frames * sizeof(TickFrame));
+  off = align256(off + pushes * sizeof(TickPush));
+  return off + poses * 12 * sizeof(double);
+}
+
+// Writes the tick being assembled (or a given frame list) into table `tab`;
+// returns the bytes used.
+size_t write_table(char* tab, const std::vector<TickFrame>& frames, const std::vector<TickPush>& pushes,
+                   const std::vector<double>& poses, int64_t n_units) {
+  TickHeader h{};
+  h.n_frames = (int32_t)frames.size();
+  h.n_pushes = (int32_t)pushes.size();
+  h.n_units = n_units;
+  h.frames_off = (int64_t)align256(sizeof(TickHeader));
+  h.pushes_off = (int64_t)align256(h.frames_off + frames.size() * sizeof(TickFrame));
+  h.poses_off = (int64_t)align256(h.pushes_off + pushes.size() * sizeof(TickPush));
+  std::memcpy(tab, &h, sizeof(h));
+  if (!frames.empty()) std::memcpy(tab + h.frames_off, frames.data(), frames.size() * sizeof(TickFrame));
+  if (!pushes.empty()) std::memcpy(tab + h.pushes_off, pushes.data(), pushes.size() * sizeof(TickPush));
+  if (!poses.empty()) std::memcpy(tab + h.poses_off, poses.data(), poses.size() * sizeof(double));
+  return (size_t)h.poses_off + poses.size() * sizeof(double);
+}
+
+// Assigns unit_begin to every frame; returns the unit count.
+int64_t number_units(std::vector<TickFrame>& frames) {
+  int64_t u = 0;
+  for (TickFrame& f : frames) {
+    f.unit_begin = u;
+    u += (int64_t)f.bands * f.groups_x;
+  }
+  return u;
+}
+
+mf::EngineKernelArgs kernel_args(mf_engine* e, int b) {
+  mf::EngineKernelArgs a{};
+  a.table = reinterpret_cast<const TickHeader*>(e->dev_tab[b]);
+  a.slots = e->slots_dev;
+  a.recs = e->recs;
+  a.max_frames = e->d.max_tick_frames;
+  return a;
+}
+
+int build_graphs(mf_engine* e) {
+  for (int b = 0; b < 2; ++b) {
+    ENG_CUDA(cudaStreamBeginCapture(e->cap_st, cudaStreamCaptureModeThreadLocal), "begin capture");
+    cudaError_t c1 = cudaMemcpyAsync(e->dev_tab[b], e->host_tab[b], e->tab_bytes,
+                                     cudaMemcpyHostToDevice, e->cap_st);
+    int64_t dummy = 0;
+    cudaError_t c2 = mf::launch_engine_tick(kernel_args(e, b), e->d.depth_dtype, e->d.map_dtype,
+                                            e->map_grid, e->cap_st, &dummy);
+    cudaGraph_t g = nullptr;
+    cudaError_t c3 = cudaStreamEndCapture(e->cap_st, &g);
+    if (c1 != cudaSuccess || c2 != cudaSuccess || c3 != cudaSuccess)
+      return fail(MF_ERR_CUDA, "tick graph capture", c1 != cudaSuccess ? c1 : (c2 != cudaSuccess ? c2 : c3));
+    e->graph[b] = g;
+    size_t n = 0;
+    ENG_CUDA(cudaGraphGetNodes(g, nullptr, &n), "graph nodes");
+    std::vector<cudaGraphNode_t> nodes(n);
+    ENG_CUDA(cudaGraphGetNodes(g, nodes.data(), &n), "graph nodes");
+    for (cudaGraphNode_t nd : nodes) {
+      cudaGraphNodeType t;
+      ENG_CUDA(cudaGraphNodeGetType(nd, &t), "graph node type");
+      if (t == cudaGraphNodeTypeMemcpy) e->copy_node[b] = nd;
+    }
+    if (!e->copy_node[b]) return fail(MF_ERR_CUDA, "tick graph has no copy node");
+    ENG_CUDA(cudaGraphInstantiate(&e->exec[b], g, 0), "graph instantiate");
+  }
+  return MF_OK;
+}
+
+void destroy(mf_engine* e) {
+  if (e->st) cudaStreamSynchronize(e->st);
+  for (auto& t : e->pending_timers) {
+    cudaEventDestroy(t.first);
+    cudaEventDestroy(t.second);
+  }
+  for (Slot& s : e->slots) {
+    if (!s.used) continue;
+    e->dfree(s.ring, (size_t)s.ring_cap * 12 * sizeof(double));
+    e->dfree(s.ring_bad, (size_t)s.ring_cap * sizeof(int32_t));
+  }
+  for (int b = 0; b < 2; ++b) {
+    if (e->exec[b]) cudaGraphExecDestroy(e->exec[b]);
+    if (e->graph[b]) cudaGraphDestroy(e->graph[b]);
+    if (e->host_tab[b]) cudaFreeHost(e->host_tab[b]);
+    e->dfree(e->dev_tab[b], e->tab_bytes);
+    if (e->done[b]) cudaEventDestroy(e->done[b]);
+    if (e->t0[b]) cudaEventDestroy(e->t0[b]);
+  }
+  e->dfree(e->recs, (size_t)e->d.max_tick_frames * sizeof(FrameRec));
+  e->dfree(e->slots_dev, (size_t)(e->d.max_streams + 1) * sizeof(SlotParams));
+  if (e->cap_st) cudaStreamDestroy(e->cap_st);
+  if (e->own_stream && e->st) cudaStreamDestroy(e->st);
+  delete e;
+}
+
+int wait_event(cudaEvent_t ev, int64_t timeout_ns) {
+  const auto t0 = std::chrono::steady_clock::now();
+  int spins = 0;
+  for (;;) {
+    const cudaError_t q = cudaEventQuery(ev);
+    if (q == cudaSuccess) return MF_OK;
+    if (q != cudaErrorNotReady) return fail(MF_ERR_CUDA, "event query", q);
+    if (timeout_ns >= 0 &&
+        std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now() - t0)
+                .count() > timeout_ns)
+      return fail(MF_ERR_TIMEOUT, "tick wait timed out");
+    if (++spins > 64)
+      std::this_thread::sleep_for(std::chrono::microseconds(20));
+    else
+      std::this_thread::yield();
+  }
+}
+
+// Waits until tick `t` and every earlier tick finished (ticks run in order).
+int wait_tick(mf_engine* e, int64_t t, int64_t timeout_ns) {
+  if (t < 0 || t >= e->next_tick) return MF_OK;
+  const int b = (int)(t & 1);
+  if (e->buf_tick[b] != t) return MF_OK;  // buffer reused: tick t finished earlier
+  return wait_event(e->done[b], timeout_ns);
+}
+
+int collect_timers(mf_engine* e) {
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> keep;
+  for (auto& t : e->pending_timers) {
+    ENG_CUDA(cudaEventSynchronize(t.second), "timer sync");
+    float ms = 0.0f;
+    ENG_CUDA(cudaEventElapsedTime(&ms, t.first, t.second), "timer elapsed");
+    e->tick_ms += ms;
+    cudaEventDestroy(t.first);
+    cudaEventDestroy(t.second);
+  }
+  e->pending_timers.clear();
+  return MF_OK;
+}
+
+void fill_slot_params(const Slot& s, const double* w, SlotParams* out) {
+  std::memset(out, 0, sizeof(*out));
+  out->ring = s.ring;
+  out->ring_bad = s.ring_bad;
+  out->ring_mask = s.ring_cap - 1;
+  out->fp.window = s.d.window;
+  out->fp.smooth_len = s.d.smooth_len;
+  out->fp.width = s.d.width;
+  out->fp.height = s.d.height;
+  out->fp.calib_width = s.d.calib_width;
+  out->fp.calib_height = s.d.calib_height;
+  out->fp.sigma_rel = s.d.sigma_rel;
+  out->fp.s_lo = s.d.s_lo;
+  out->fp.s_hi = s.d.s_hi;
+  out->d0 = (float)s.d.depth_ref_m;
+  for (int k = 0; k < mf::kMaxHist; ++k) out->w[k] = k < s.d.smooth_len ? w[k] : 0.0;
+}
+
+// Candidate tile heights for a frame height: divisions of the height into
+// equal bands no taller than each nominal value.
+std::vector<int> band_candidates(int height) {
+  std::vector<int> out;
+  for (int nominal : {32, 64, 96, 128, 192, 256}) {
+    const int bands = (height + nominal - 1) / nominal;
+    const int bh = (height + bands - 1) / bands;
+    if (std::find(out.begin(), out.end(), bh) == out.end()) out.push_back(bh);
+  }
+  return out;
+}
+
+int tune_class(mf_engine* e, int width, int height, int window, int* band_out) {
+  const auto key = std::make_tuple(width, height, window);
+  auto it = e->tuned.find(key);
+  if (it != e->tuned.end()) {
+    *band_out = it->second;
+    return MF_OK;
+  }
+  ENG_CUDA(cudaStreamSynchronize(e->st), "stream sync before tuning");
+  const size_t px = (size_t)width * height;
+  const size_t per_frame = px * (dtype_bytes(e->d.depth_dtype) + 2 * dtype_bytes(e->d.map_dtype));
+  int frames = (int)std::max<size_t>(2, std::min<size_t>(64, ((size_t)1 << 30) / per_frame));
+  frames = std::min(frames, e->d.max_tick_frames);
+  char* buf = (char*)e->dalloc(per_frame * frames);
+  if (!buf) return fail(MF_ERR_OOM, "tuning buffers");
+  ENG_CUDA(cudaMemsetAsync(buf, 0, per_frame * frames, e->st), "tuning memset");
+  // synthetic worst case: `window` points spread inside the frame
+  std::vector<FrameRec> recs(frames);
+  const double fx = 0.9 * width;
+  for (int f = 0; f < frames; ++f) {
+    FrameRec& r = recs[f];
+    std::memset(&r, 0, sizeof(r));
+    const int n = std::min(window, (int)mf::kMaxPts);
+    r.n_valid = n;
+    r.inv_n = (float)(1.0 / n);
+    for (int i = 0; i < n; ++i) {
+      const double fu = std::fmod(0.1 + 0.618034 * (i + 3 * f), 1.0);
+      const double fv = std::fmod(0.2 + 0.414214 * (i + 5 * f), 1.0);
+      const double sig = 0.1 * fx * (0.5 + fu);
+      r.ux_hi[i] = (float)(width * (0.1 + 0.8 * fu));
+      r.vy_hi[i] = (float)(height * (0.1 + 0.8 * fv));
+      const double c = 1.0 / (2.0 * sig * sig);
+      r.c_hi[i] = (float)c;
+      r.c_lo[i] = (float)(c - (double)(float)c);
+    }
+  }
+  ENG_CUDA(cudaMemcpyAsync(e->recs, recs.data(), sizeof(FrameRec) * frames, cudaMemcpyHostToDevice, e->st),
+           "tuning records");
+  Slot tmp;
+  tmp.d.width = width;
+  tmp.d.height = height;
+  tmp.d.window = window;
+  tmp.d.depth_ref_m = 1.0;
+  SlotParams sp;
+  double w[mf::kMaxHist] = {};
+  fill_slot_params(tmp, w, &sp);
+  ENG_CUDA(cudaMemcpyAsync(e->slots_dev + e->d.max_streams, &sp, sizeof(sp), cudaMemcpyHostToDevice, e->st),
+           "tuning slot");
+  const size_t pin = per_frame / (dtype_bytes(e->d.depth_dtype) + 2 * dtype_bytes(e->d.map_dtype));
+  cudaEvent_t a, b2;
+  ENG_CUDA(cudaEventCreate(&a), "event");
+  ENG_CUDA(cudaEventCreate(&b2), "event");
+  int best_band = default_band(height);
+  float best_ms = 1e30f;
+  std::vector<TickPush> pushes(1);
+  pushes[0].slot = e->d.max_streams;
+  std::vector<double> no_poses;
+  for (int bh : band_candidates(height)) {
+    std::vector<TickFrame> frs(frames);
+    for (int f = 0; f < frames; ++f) {
+      TickFrame& t = frs[f];
+      std::memset(&t, 0, sizeof(t));
+      t.push = 0;
+      t.k = f;
+      t.bucket = window;
+      t.band_h = bh;
+      t.bands = (height + bh - 1) / bh;
+      t.groups_x = (width + mf::kEngineGroupW - 1) / mf::kEngineGroupW;
+      char* base = buf + (size_t)f * per_frame;
+      t.depth = base;
+      t.M = base + pin * dtype_bytes(e->d.depth_dtype);
+      t.G = t.M + pin * dtype_bytes(e->d.map_dtype);
+      t.info = nullptr;
+    }
+    const int64_t units = number_units(frs);
+    const size_t used = write_table(e->host_tab[0], frs, pushes, no_poses, units);
+    ENG_CUDA(cudaMemcpyAsync(e->dev_tab[0], e->host_tab[0], used, cudaMemcpyHostToDevice, e->st), "table");
+    const mf::EngineKernelArgs args = kernel_args(e, 0);
+    ENG_CUDA(mf::launch_engine_map_only(args, e->d.depth_dtype, e->d.map_dtype, e->map_grid, e->st), "tune");
+    ENG_CUDA(cudaEventRecord(a, e->st), "event");
+    for (int rep = 0; rep < 3; ++rep)
+      ENG_CUDA(mf::launch_engine_map_only(args, e->d.depth_dtype, e->d.map_dtype, e->map_grid, e->st), "tune");
+    ENG_CUDA(cudaEventRecord(b2, e->st), "event");
+    ENG_CUDA(cudaEventSynchronize(b2), "event");
+    float ms = 0.0f;
+    ENG_CUDA(cudaEventElapsedTime(&ms, a, b2), "elapsed");
+    e->launches += 4;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best_band = bh;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b2);
+  ENG_CUDA(cudaStreamSynchronize(e->st), "stream sync after tuning");
+  e->dfree(buf, per_frame * frames);
+  e->buf_tick[0] = -1;  // the table buffer held tuning data
+  e->tuned[key] = best_band;
+  *band_out = best_band;
+  return MF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void mf_engine_desc_init(mf_engine_desc* d) {
+  if (!d) return;
+  std::memset(d, 0, sizeof(*d));
+  d->max_streams = 256;
+  d->max_tick_frames = 4096;
+  d->max_stream_frames = 64;
+  d->depth_dtype = MF_F32;
+  d->map_dtype = MF_F32;
+}
+
+int mf_engine_open(const mf_engine_desc* d, mf_engine** out) {
+  if (!out || !d) return fail(MF_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  if (d->max_streams < 1 || d->max_streams > 65536 || d->max_tick_frames < 1 ||
+      d->max_tick_frames > (1 << 20) || d->max_stream_frames < 1 ||
+      d->max_stream_frames > d->max_tick_frames || d->memory_budget < 0)
+    return fail(MF_ERR_INVALID_ARG, "engine limits out of range");
+  for (int dt : {d->depth_dtype, d->map_dtype})
+    if (dt != MF_F32 && dt != MF_BF16 && dt != MF_F16) return fail(MF_ERR_INVALID_ARG, "unknown dtype");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+    cudaGetLastError();
+    return fail(MF_ERR_NO_DEVICE, "no CUDA device");
+  }
+  mf_engine* e = new (std::nothrow) mf_engine();
+  if (!e) return fail(MF_ERR_OOM, "host allocation");
+  e->d = *d;
+  cudaGetDevice(&e->device);
+  e->slots.resize(d->max_streams);
+  if (d->cuda_stream) {
+    e->st = (cudaStream_t)d->cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&e->st, cudaStreamNonBlocking) != cudaSuccess) {
+      delete e;
+      return fail(MF_ERR_CUDA, "stream creation");
+    }
+    e->own_stream = true;
+  }
+  if (cudaStreamCreateWithFlags(&e->cap_st, cudaStreamNonBlocking) != cudaSuccess) {
+    destroy(e);
+    return fail(MF_ERR_CUDA, "capture stream creation");
+  }
+  e->slots_dev = (SlotParams*)e->dalloc((size_t)(d->max_streams + 1) * sizeof(SlotParams));
+  e->recs = (FrameRec*)e->dalloc((size_t)d->max_tick_frames * sizeof(FrameRec));
+  e->tab_bytes = table_bytes(d->max_tick_frames, d->max_streams, e->poses_cap());
+  for (int b = 0; b < 2; ++b) {
+    e->dev_tab[b] = (char*)e->dalloc(e->tab_bytes);
+    if (cudaMallocHost(&e->host_tab[b], e->tab_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      e->host_tab[b] = nullptr;
+    }
+    if (cudaEventCreateWithFlags(&e->done[b], cudaEventDisableTiming) != cudaSuccess) e->done[b] = nullptr;
+  }
+  if (!e->slots_dev || !e->recs || !e->dev_tab[0] || !e->dev_tab[1] || !e->host_tab[0] ||
+      !e->host_tab[1] || !e->done[0] || !e->done[1]) {
+    destroy(e);
+    return fail(MF_ERR_OOM, "engine allocation");
+  }
+  if (d->memory_budget > 0 && e->device_bytes > d->memory_budget) {
+    destroy(e);
+    return fail(MF_ERR_ADMISSION, "engine tables exceed the memory budget");
+  }
+  e->map_grid = mf::engine_map_grid(d->depth_dtype, d->map_dtype);
+  // an empty table in both buffers, so a graph replay with nothing to do is harmless
+  for (int b = 0; b < 2; ++b) {
+    std::vector<TickFrame> nf;
+    std::vector<TickPush> np;
+    std::vector<double> npo;
+    const size_t used = write_table(e->host_tab[b], nf, np, npo, 0);
+    if (cudaMemcpy(e->dev_tab[b], e->host_tab[b], used, cudaMemcpyHostToDevice) != cudaSuccess) {
+      destroy(e);
+      return fail(MF_ERR_CUDA, "table init");
+    }
+  }
+  if (!(d->flags & MF_ENGINE_NO_GRAPH)) {
+    const int rc = build_graphs(e);
+    if (rc) {
+      destroy(e);
+      return rc;
+    }
+  }
+  *out = e;
+  return MF_OK;
+}
+
+int mf_engine_add_stream(mf_engine* e, const mf_stream_desc* d, int64_t reserve_bytes, int32_t* slot) {
+  if (!e || !d || !slot) return fail(MF_ERR_INVALID_ARG, "NULL argument");
+  *slot = -1;
+  int rc = mf::host_validate_desc(d);
+  if (rc) return rc;
+  if (d->depth_dtype != e->d.depth_dtype || d->map_dtype != e->d.map_dtype)
+    return fail(MF_ERR_INVALID_ARG, "stream dtypes differ from the engine's");
+  if (reserve_bytes < 0) return fail(MF_ERR_INVALID_ARG, "negative reservation");
+  if (d->width % mf::kEngineCPT) return fail(MF_ERR_INVALID_ARG, "engine streams need an even width");
+  int free_slot = -1;
+  for (int i = 0; i < e->d.max_streams; ++i)
+    if (!e->slots[i].used) {
+      free_slot = i;
+      break;
+    }
+  if (free_slot < 0) return fail(MF_ERR_ADMISSION, "every stream slot is taken");
+  const int64_t cap = pow2_at_least(std::max<int64_t>(
+      128, (int64_t)d->window + d->smooth_len - 1 + e->d.max_stream_frames));
+  const int64_t need = cap * (12 * (int64_t)sizeof(double) + (int64_t)sizeof(int32_t)) + reserve_bytes;
+  if (e->d.memory_budget > 0 && e->accounted() + need > e->d.memory_budget)
+    return fail(MF_ERR_ADMISSION, "device memory budget exhausted");
+  double w[mf::kMaxHist] = {};
+  if (!mf::host_ls_weights(d->smooth_len, d->mode, w))
+    return fail(MF_ERR_INVALID_ARG, "least-squares weights not representable");
+  DeviceGuard guard(e->device);
+  int band = default_band(d->height);
+  if (!(e->d.flags & MF_ENGINE_NO_TUNE)) {
+    rc = tune_class(e, d->width, d->height, std::min(d->window, (int)mf::kMaxPts), &band);
+    if (rc) return rc;
+  }
+  Slot& s = e->slots[free_slot];
+  s = Slot();
+  s.d = *d;
+  s.ring_cap = cap;
+  s.ring = (double*)e->dalloc((size_t)cap * 12 * sizeof(double));
+  s.ring_bad = (int32_t*)e->dalloc((size_t)cap * sizeof(int32_t));
+  if (!s.ring || !s.ring_bad) {
+    e->dfree(s.ring, (size_t)cap * 12 * sizeof(double));
+    e->dfree(s.ring_bad, (size_t)cap * sizeof(int32_t));
+    s = Slot();
+    return fail(MF_ERR_OOM, "pose history allocation");
+  }
+  s.reserve = reserve_bytes;
+  s.plane_in = (size_t)d->width * d->height * dtype_bytes(d->depth_dtype);
+  s.plane_out = (size_t)d->width * d->height * dtype_bytes(d->map_dtype);
+  s.band_h = band;
+  s.bands = (d->height + band - 1) / band;
+  s.groups_x = (d->width + mf::kEngineGroupW - 1) / mf::kEngineGroupW;
+  SlotParams sp;
+  fill_slot_params(s, w, &sp);
+  ENG_CUDA(cudaMemcpyAsync(e->slots_dev + free_slot, &sp, sizeof(sp), cudaMemcpyHostToDevice, e->st),
+           "slot upload");
+  ENG_CUDA(cudaStreamSynchronize(e->st), "slot upload");
+  s.used = true;
+  *slot = free_slot;
+  return MF_OK;
+}
+
+int mf_engine_remove_stream(mf_engine* e, int32_t slot) {
+  if (!e || slot < 0 || slot >= e->d.max_streams || !e->slots[slot].used)
+    return fail(MF_ERR_INVALID_ARG, "no such stream");
+  Slot& s = e->slots[slot];
+  if (s.pending_tick == e->next_tick) return fail(MF_ERR_INVALID_ARG, "the stream has a queued push");
+  DeviceGuard guard(e->device);
+  int rc = wait_tick(e, s.last_tick, -1);
+  if (rc) return rc;
+  e->dfree(s.ring, (size_t)s.ring_cap * 12 * sizeof(double));
+  e->dfree(s.ring_bad, (size_t)s.ring_cap * sizeof(int32_t));
+  s = Slot();
+  return MF_OK;
+}
+
+int mf_engine_submit(mf_engine* e, int32_t slot, int32_t n, const double* poses, const void* depth,
+                     const double* K, void* focus_map, void* guided_depth, mf_frame_info* info) {
+  if (!e || slot < 0 || slot >= e->d.max_streams || !e->slots[slot].used)
+    return fail(MF_ERR_INVALID_ARG, "no such stream");
+  Slot& s = e->slots[slot];
+  if (n < 1 || !poses || !K) return fail(MF_ERR_INVALID_ARG, "n < 1 or NULL poses/K");
+  if (s.pending_tick == e->next_tick) return fail(MF_ERR_NOT_READY, "the stream already has a push in this tick");
+  const bool local = s.d.pose_frame == MF_POSES_BATCH_LOCAL;
+  const int O = (local && s.pushes > 0) ? s.d.overlap : 0;
+  if (n <= O) return fail(MF_ERR_INVALID_ARG, "batch must hold more frames than the overlap");
+  const int n_emit = n - O;
+  if (n_emit > e->d.max_stream_frames) return fail(MF_ERR_INVALID_ARG, "push exceeds max_stream_frames");
+  if ((int64_t)e->frames.size() + n_emit > e->d.max_tick_frames)
+    return fail(MF_ERR_NOT_READY, "the tick is full: call mf_engine_tick");
+  for (int k = 0; k < 4; ++k)
+    if (!std::isfinite(K[k])) return fail(MF_ERR_INVALID_ARG, "non-finite intrinsics");
+  if (!(K[0] > 0.0) || !(K[1] > 0.0)) return fail(MF_ERR_INVALID_ARG, "fx, fy must be > 0");
+  DeviceGuard guard(e->device);
+  if (on_device(poses)) return fail(MF_ERR_INVALID_ARG, "engine poses must be host memory");
+  for (const void* p : {depth, (const void*)focus_map, (const void*)guided_depth, (const void*)info})
+    if (p && !on_device(p)) return fail(MF_ERR_INVALID_ARG, "engine planes and records must be device memory");
+  // two pixels per lane access: planes aligned to two elements
+  if ((depth && (uintptr_t)depth % (2 * dtype_bytes(e->d.depth_dtype))) ||
+      (focus_map && (uintptr_t)focus_map % (2 * dtype_bytes(e->d.map_dtype))) ||
+      (guided_depth && (uintptr_t)guided_depth % (2 * dtype_bytes(e->d.map_dtype))) ||
+      (info && (uintptr_t)info % 8))
+    return fail(MF_ERR_INVALID_ARG, "misaligned plane or record pointer");
+  TickPush ps{};
+  ps.slot = slot;
+  ps.n = n;
+  ps.first = O;
+  ps.anchor = O > 0 ? 1 : 0;
+  ps.e0 = s.emitted;
+  ps.pose_off = (int64_t)(e->poses.size() / 12);
+  for (int k = 0; k < 4; ++k) ps.K[k] = K[k];
+  const int push_idx = (int)e->pushes.size();
+  e->pushes.push_back(ps);
+  e->poses.insert(e->poses.end(), poses, poses + (size_t)n * 12);
+  for (int k = 0; k < n_emit; ++k) {
+    TickFrame t{};
+    t.push = push_idx;
+    t.k = k;
+    t.bucket = s.d.window;
+    t.band_h = s.band_h;
+    t.bands = s.bands;
+    t.groups_x = s.groups_x;
+    t.depth = depth ? static_cast<const char*>(depth) + (size_t)(O + k) * s.plane_in : nullptr;
+    t.M = focus_map ? static_cast<char*>(focus_map) + (size_t)k * s.plane_out : nullptr;
+    t.G = guided_depth ? static_cast<char*>(guided_depth) + (size_t)k * s.plane_out : nullptr;
+    t.info = info ? info + k : nullptr;
+    e->frames.push_back(t);
+  }
+  s.emitted += n_emit;
+  ++s.pushes;
+  s.pending_tick = e->next_tick;
+  s.last_tick = e->next_tick;
+  return MF_OK;
+}
+
+int mf_engine_tick(mf_engine* e, int64_t* tick) {
+  if (!e || !tick) return fail(MF_ERR_INVALID_ARG, "NULL argument");
+  *tick = -1;
+  if (e->frames.empty()) return MF_OK;
+  DeviceGuard guard(e->device);
+  const int64_t t = e->next_tick;
+  const int b = (int)(t & 1);
+  // the buffer's previous tick must have consumed its table
+  if (e->buf_tick[b] >= 0) {
+    const int rc = wait_event(e->done[b], -1);
+    if (rc) return rc;
+  }
+  const int64_t units = number_units(e->frames);
+  const size_t used = write_table(e->host_tab[b], e->frames, e->pushes, e->poses, units);
+  cudaEvent_t ta = nullptr, tb = nullptr;
+  if (e->d.flags & MF_FLAG_TIME_KERNELS) {
+    ENG_CUDA(cudaEventCreate(&ta), "event");
+    ENG_CUDA(cudaEventCreate(&tb), "event");
+    ENG_CUDA(cudaEventRecord(ta, e->st), "event");
+  }
+  if (e->exec[b]) {
+    ENG_CUDA(cudaGraphExecMemcpyNodeSetParams1D(e->exec[b], e->copy_node[b], e->dev_tab[b],
+                                                e->host_tab[b], used, cudaMemcpyHostToDevice),
+             "graph copy update");
+    ENG_CUDA(cudaGraphLaunch(e->exec[b], e->st), "graph launch");
+    ++e->graph_launches;
+    e->launches += 4;
+  } else {
+    ENG_CUDA(cudaMemcpyAsync(e->dev_tab[b], e->host_tab[b], used, cudaMemcpyHostToDevice, e->st), "table");
+    ENG_CUDA(mf::launch_engine_tick(kernel_args(e, b), e->d.depth_dtype, e->d.map_dtype, e->map_grid,
+                                    e->st, &e->launches),
+             "tick launch");
+  }
+  mf::host_count_launches(4);
+  if (ta) {
+    ENG_CUDA(cudaEventRecord(tb, e->st), "event");
+    e->pending_timers.emplace_back(ta, tb);
+  }
+  ENG_CUDA(cudaEventRecord(e->done[b], e->st), "event");
+  e->buf_tick[b] = t;
+  ++e->ticks;
+  e->frames_done += (int64_t)e->frames.size();
+  e->units_done += units;
+  e->frames.clear();
+  e->pushes.clear();
+  e->poses.clear();
+  e->next_tick = t + 1;
+  *tick = t;
+  return MF_OK;
+}
+
+int mf_engine_query(mf_engine* e, int64_t tick, int32_t* done) {
+  if (!e || !done) return fail(MF_ERR_INVALID_ARG, "NULL argument");
+  *done = 1;
+  if (tick < 0 || tick >= e->next_tick) return MF_OK;
+  const int b = (int)(tick & 1);
+  if (e->buf_tick[b] != tick) return MF_OK;
+  DeviceGuard guard(e->device);
+  const cudaError_t q = cudaEventQuery(e->done[b]);
+  if (q == cudaErrorNotReady) {
+    *done = 0;
+    return MF_OK;
+  }
+  if (q != cudaSuccess) return fail(MF_ERR_CUDA, "event query", q);
+  return MF_OK;
+}
+
+int mf_engine_wait(mf_engine* e, int64_t tick, int64_t timeout_ns) {
+  if (!e) return fail(MF_ERR_INVALID_ARG, "NULL engine");
+  DeviceGuard guard(e->device);
+  return wait_tick(e, tick, timeout_ns);
+}
+
+int mf_engine_tune(mf_engine* e, int32_t width, int32_t height, int32_t window, int32_t* band_h) {
+  if (!e || !band_h || width < 1 || height < 1 || width > MF_MAX_DIM || height > MF_MAX_DIM ||
+      window < 1 || window > MF_MAX_WINDOW)
+    return fail(MF_ERR_INVALID_ARG, "bad tuning request");
+  if (!e->frames.empty()) return fail(MF_ERR_NOT_READY, "a tick is being assembled");
+  DeviceGuard guard(e->device);
+  e->tuned.erase(std::make_tuple(width, height, window));
+  return tune_class(e, width, height, window, band_h);
+}
+
+int mf_engine_get_stats(mf_engine* e, mf_engine_stats* out) {
+  if (!e || !out) return fail(MF_ERR_INVALID_ARG, "NULL argument");
+  DeviceGuard guard(e->device);
+  int rc = collect_timers(e);
+  if (rc) return rc;
+  std::memset(out, 0, sizeof(*out));
+  out->ticks = e->ticks;
+  out->frames = e->frames_done;
+  out->units = e->units_done;
+  out->kernel_launches = e->launches;
+  out->graph_launches = e->graph_launches;
+  int n = 0;
+  for (const Slot& s : e->slots) n += s.used ? 1 : 0;
+  out->streams = n;
+  out->device_bytes = e->device_bytes;
+  out->accounted_bytes = e->accounted();
+  out->tick_gpu_ms = e->tick_ms;
+  return MF_OK;
+}
+
+int mf_engine_close(mf_engine* e) {
+  if (!e) return MF_OK;
+  DeviceGuard guard(e->device);
+  destroy(e);
+  return MF_OK;
+}
+
+}  // extern "C"

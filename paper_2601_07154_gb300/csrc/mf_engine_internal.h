@@ -1,0 +1,74 @@
+// Tick tables shared by the engine host code (mf_engine.cpp) and its batched
+// kernels (mf_engine_kernels.cu).  Not part of the public ABI.
+#pragma once
+
+#include "mf_internal.h"
+#include "mf_pose_device.cuh"
+
+namespace mf {
+
+constexpr int kEngineCPT = 2;                           // columns per lane in the batched map
+constexpr int kEngineGroupW = 8 * 32 * kEngineCPT;      // columns per map unit
+
+// Per admitted stream, written once at admission (device array by slot).
+struct SlotParams {
+  double* ring;            // resident pose history, ring_mask+1 slots x 12
+  int32_t* ring_bad;
+  int64_t ring_mask;
+  FrameParams fp;
+  float d0;
+  int32_t pad;
+  double w[kMaxHist];      // least-squares weights
+};
+
+// One push of one stream in a tick.
+struct TickPush {
+  int32_t slot;
+  int32_t n;               // poses in the push
+  int32_t first;           // first emitted pose (overlap or 0)
+  int32_t anchor;          // gravity-locked anchoring against the history
+  int64_t e0;              // stream's emitted count before the push
+  int64_t pose_off;        // index of the push's first pose in the tick's pose block
+  double K[4];
+};
+
+// One emitted frame of a tick (frames of a push are consecutive).
+struct TickFrame {
+  int32_t push;            // index into the tick's pushes
+  int32_t k;               // emitted offset within the push
+  int32_t bucket;          // window of the stream (informational)
+  int32_t band_h;          // tile height (autotuned per resolution class)
+  int32_t groups_x;        // strip groups across the frame
+  int32_t bands;
+  int64_t unit_begin;      // first map unit of the frame
+  const char* depth;       // depth plane (device) or NULL
+  char* M;                 // focus-map plane (device) or NULL
+  char* G;                 // guided-depth plane (device) or NULL
+  mf_frame_info* info;     // record (device) or NULL
+};
+
+// Layout of one tick table (header, frames, pushes, poses; each 256-B aligned).
+struct TickHeader {
+  int32_t n_frames, n_pushes;
+  int64_t n_units;
+  int64_t frames_off, pushes_off, poses_off;  // byte offsets from the header
+  int64_t pad[3];
+};
+
+struct EngineKernelArgs {
+  const TickHeader* table;     // device tick table
+  const SlotParams* slots;     // device slot parameters
+  FrameRec* recs;              // max_tick_frames records
+  int max_frames;              // capacity (grid sizes of the per-frame kernels)
+};
+
+cudaError_t launch_engine_tick(const EngineKernelArgs& a, int depth_dtype, int map_dtype,
+                               int map_grid, cudaStream_t st, int64_t* launches);
+// Resident CTAs per SM x SMs for the batched map kernel of a dtype pair.
+int engine_map_grid(int depth_dtype, int map_dtype);
+size_t engine_map_smem();
+// Times the batched map kernel over the given table (already on the device).
+cudaError_t launch_engine_map_only(const EngineKernelArgs& a, int depth_dtype, int map_dtype,
+                                   int map_grid, cudaStream_t st);
+
+}  // namespace mf

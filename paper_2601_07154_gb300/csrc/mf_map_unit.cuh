@@ -30,9 +30,6 @@
 
 namespace mf {
 
-constexpr int kStages = 6;       // depth rows in flight per warp
-constexpr int kBandMax = 256;    // rows per unit
-constexpr int kGroupStrips = 8;  // strips (one per warp) per unit
 constexpr float kCullBelow = 9.094947017729282e-13f;  // 2^-40
 
 template <int NMAX>

@@ -133,3 +133,90 @@ class MotionFocusStream:
             self.close()
         except Exception:
             pass
+
+
+class MotionFocusEngine:
+    """Many streams processed in batched ticks (the C ABI's mf_engine_*).
+
+    ``add_stream`` admits a stream (its pose history lives on the GPU);
+    ``submit`` queues one push of a stream with the device planes its maps
+    go to; ``tick`` launches everything queued as one batch (a CUDA graph)
+    without waiting.
+    """
+
+    def __init__(self, max_streams=256, max_tick_frames=4096, max_stream_frames=64,
+                 depth_dtype=torch.float32, map_dtype=torch.float32, memory_budget=0,
+                 graph=True, tune=True, time_kernels=False, device=None, cuda_stream=None):
+        self.device = torch.device(device) if device is not None else torch.device(
+            "cuda", torch.cuda.current_device())
+        self.depth_dtype, self.map_dtype = depth_dtype, map_dtype
+        flags = 0 if graph else _mf.MF_ENGINE_NO_GRAPH
+        flags |= 0 if tune else _mf.MF_ENGINE_NO_TUNE
+        flags |= _mf.MF_FLAG_TIME_KERNELS if time_kernels else 0
+        with torch.cuda.device(self.device):
+            self.torch_stream = cuda_stream or torch.cuda.current_stream(self.device)
+            self.desc = _mf.mf_engine_desc_init(
+                max_streams=max_streams, max_tick_frames=max_tick_frames,
+                max_stream_frames=max_stream_frames, depth_dtype=_DT[depth_dtype],
+                map_dtype=_DT[map_dtype], flags=flags, memory_budget=int(memory_budget),
+                cuda_stream=self.torch_stream.cuda_stream or 1)
+            self.handle = _mf.mf_engine_open(self.desc)
+        self.streams = {}
+
+    def add_stream(self, width, height, window=8, smooth_len=15, mode="accel",
+                   pose_frame="world", overlap=0, calib=None, reserve_bytes=0, sigma_rel=0.1,
+                   s_lo=0.25, s_hi=4.0, depth_ref_m=1.0):
+        cw, ch = calib if calib is not None else (0, 0)
+        d = _mf.mf_stream_desc_init(
+            width=int(width), height=int(height), calib_width=cw, calib_height=ch,
+            window=int(window), smooth_len=int(smooth_len), mode=_MODES[mode],
+            pose_frame=_FRAMES[pose_frame], overlap=int(overlap),
+            depth_dtype=_DT[self.depth_dtype], map_dtype=_DT[self.map_dtype],
+            sigma_rel=sigma_rel, s_lo=s_lo, s_hi=s_hi, depth_ref_m=depth_ref_m)
+        with torch.cuda.device(self.device):
+            slot = _mf.mf_engine_add_stream(self.handle, d, reserve_bytes)
+        self.streams[slot] = (int(width), int(height), int(window))
+        return slot
+
+    def remove_stream(self, slot):
+        with torch.cuda.device(self.device):
+            _mf.mf_engine_remove_stream(self.handle, slot)
+        self.streams.pop(slot, None)
+
+    def submit(self, slot, poses, depth, K, focus_map=None, guided_depth=None, info=None):
+        """poses: host (n,3,4) FP64; depth / maps / info: device tensors or None."""
+        P = np.ascontiguousarray(np.asarray(poses, dtype=np.float64))
+        Kh = np.ascontiguousarray(np.asarray(K, dtype=np.float64).reshape(4))
+        with torch.cuda.device(self.device):
+            _mf.mf_engine_submit(self.handle, slot, P.shape[0], P, depth, Kh, focus_map,
+                                 guided_depth, info)
+
+    def tick(self):
+        with torch.cuda.device(self.device):
+            return _mf.mf_engine_tick(self.handle)
+
+    def done(self, tick):
+        return _mf.mf_engine_query(self.handle, tick)
+
+    def wait(self, tick, timeout_ns=-1):
+        with torch.cuda.device(self.device):
+            _mf.mf_engine_wait(self.handle, tick, timeout_ns)
+
+    def tune(self, width, height, window):
+        with torch.cuda.device(self.device):
+            return _mf.mf_engine_tune(self.handle, width, height, window)
+
+    def stats(self):
+        return _mf.mf_engine_get_stats(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            with torch.cuda.device(self.device):
+                _mf.mf_engine_close(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

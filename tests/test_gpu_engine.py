@@ -1,0 +1,249 @@
+"""The batched engine: parity with the oracle over a mix of streams, identical
+results alone and in the mix, graph vs direct launches, admission, tuning."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O  # noqa: E402
+from synth import WalkerSpec, small_stream, walk  # noqa: E402
+from tests import parity  # noqa: E402
+from tests.posegen import rot_x, rot_y, trajectory  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    import paper_2601_07154_gb300 as m
+    return m
+
+
+def _accelerating_walk(n, seed=0):
+    rng = np.random.default_rng(seed)
+    cs, rs = [], []
+    for k in range(n):
+        t = k / 30.0
+        cs.append(np.array([0.05 * math.sin(2.0 * t + seed), 0.02 * math.sin(3.1 * t),
+                            1.0 * t + 0.6 * t * t]) + rng.normal(0, 1e-4, 3))
+        rs.append(rot_y(0.2 * math.sin(1.3 * t + seed)) @ rot_x(0.05 * math.sin(4 * t)))
+    return trajectory(cs, rs)
+
+
+# (width, height, window, smooth_len, mode, seed, frames)
+STREAMS = [
+    (320, 240, 8, 15, "heading", 1, 40),
+    (256, 144, 16, 7, "accel", 2, 37),
+    (192, 108, 32, 3, "accel", 3, 45),
+    (130, 70, 5, 5, "heading", 4, 33),
+    (64, 48, 12, 9, "accel", 5, 41),
+]
+
+
+def _inputs(spec):
+    width, height, window, smooth_len, mode, seed, frames = spec
+    if mode == "heading" and seed == 1:
+        w = small_stream(seed=seed, n_frames=frames, window=window, smooth_len=smooth_len)
+        poses, depth, K = w.poses, w.depth_stack(0, frames), w.K()
+    else:
+        poses = _accelerating_walk(frames, seed)
+        rng = np.random.default_rng(seed)
+        depth = rng.uniform(0.2, 5.0, (frames, height, width)).astype(np.float32)
+        K = np.array([0.9 * width, 0.9 * width, (width - 1) / 2.0, (height - 1) / 2.0])
+    return poses, depth, K
+
+
+def _run_engine(mf, specs, chunk=7, graph=True, tune=True, only=None):
+    """Feed each stream in chunks, one push per stream per tick; returns per-stream outputs."""
+    dev = torch.device("cuda", 0)
+    eng = mf.MotionFocusEngine(max_streams=8, max_tick_frames=512, max_stream_frames=16,
+                               graph=graph, tune=tune, device=dev)
+    state = []
+    for idx, spec in enumerate(specs):
+        if only is not None and idx not in only:
+            state.append(None)
+            continue
+        width, height, window, smooth_len, mode, seed, frames = spec
+        poses, depth, K = _inputs(spec)
+        slot = eng.add_stream(width, height, window=window, smooth_len=smooth_len, mode=mode)
+        M = torch.zeros((frames, height, width), device=dev)
+        G = torch.zeros_like(M)
+        info = torch.zeros(frames * 64, dtype=torch.uint8, device=dev)
+        state.append(dict(slot=slot, poses=poses, depth=torch.from_numpy(depth).to(dev), K=K,
+                          M=M, G=G, info=info, next=0, frames=frames))
+    ticks = []
+    while any(s is not None and s["next"] < s["frames"] for s in state):
+        for s in state:
+            if s is None or s["next"] >= s["frames"]:
+                continue
+            lo, hi = s["next"], min(s["frames"], s["next"] + chunk)
+            infoview = s["info"][lo * 64:hi * 64]
+            eng.submit(s["slot"], s["poses"][lo:hi], s["depth"][lo:hi], s["K"], s["M"][lo:hi],
+                       s["G"][lo:hi], infoview)
+            s["next"] = hi
+        ticks.append(eng.tick())
+    eng.wait(ticks[-1])
+    stats = eng.stats()
+    out = []
+    for s in state:
+        if s is None:
+            out.append(None)
+            continue
+        out.append((s["M"].cpu().numpy(), s["G"].cpu().numpy(),
+                    s["info"].cpu().numpy().view(mf.FRAME_INFO_DTYPE)))
+    eng.close()
+    return out, stats
+
+
+def test_engine_mixed_streams_match_oracle(mf):
+    outs, stats = _run_engine(mf, STREAMS)
+    assert stats.ticks >= 6 and stats.frames == sum(s[6] for s in STREAMS)
+    assert stats.graph_launches == stats.ticks
+    for spec, (M, G, info) in zip(STREAMS, outs):
+        width, height, window, smooth_len, mode, seed, frames = spec
+        poses, depth, K = _inputs(spec)
+        ref = O.OracleStream(O.Params(width, height, window=window, smooth_len=smooth_len,
+                                      mode=O.MODE_ACCEL if mode == "accel" else O.MODE_HEADING))
+        ref.push(poses, depth.astype(np.float64), K)
+        intr = O.compensated_intrinsics(K, ref.p)
+        for n in range(frames):
+            rinfo, rp, Mr, Gr = ref.frame(n)
+            parity.check_frame(info[n], None, rinfo, rp, intr, where=f"{spec} frame {n}")
+            parity.check_map(M[n], Mr, where=f"{spec} M {n}")
+            parity.check_map(G[n], Gr, where=f"{spec} G {n}")
+            parity.check_argmax(info[n], Mr, rinfo["n_valid"], where=f"{spec} argmax {n}")
+        assert info["n_valid"].sum() > 0
+
+
+def test_engine_alone_and_mixed_identical(mf):
+    mixed, _ = _run_engine(mf, STREAMS)
+    for idx in (0, 2, 4):
+        alone, _ = _run_engine(mf, STREAMS, only={idx})
+        for a, b in zip(alone[idx], mixed[idx]):
+            assert np.array_equal(a, b), STREAMS[idx]
+
+
+def test_engine_graph_and_direct_launches_identical(mf):
+    a, sa = _run_engine(mf, STREAMS[:3], graph=True)
+    b, sb = _run_engine(mf, STREAMS[:3], graph=False)
+    assert sa.graph_launches > 0 and sb.graph_launches == 0
+    for x, y in zip(a, b):
+        for u, v in zip(x, y):
+            assert np.array_equal(u, v)
+
+
+def test_engine_untuned_matches_oracle_tolerance(mf):
+    tuned, _ = _run_engine(mf, STREAMS[:2], tune=True)
+    plain, _ = _run_engine(mf, STREAMS[:2], tune=False)
+    for x, y in zip(tuned, plain):
+        # tile heights may differ: maps agree to the map tolerance, records exactly
+        assert np.all(np.abs(x[0] - y[0]) <= 1e-5 * np.abs(y[0]) + 1e-10)
+        for k in parity.INT_FIELDS:
+            assert np.array_equal(x[2][k], y[2][k])
+
+
+def test_engine_admission_by_memory_and_slots(mf):
+    dev = torch.device("cuda", 0)
+    probe = mf.MotionFocusEngine(max_streams=2, max_tick_frames=64, max_stream_frames=8, device=dev)
+    a = probe.add_stream(64, 48, window=8, smooth_len=5)
+    probe.add_stream(64, 48, window=8, smooth_len=5)
+    with pytest.raises(mf.MFError) as e:
+        probe.add_stream(64, 48)
+    assert e.value.status == mf.MF_ERR_ADMISSION          # slots exhausted
+    probe.remove_stream(a)
+    probe.add_stream(64, 48, window=8, smooth_len=5)       # the freed slot is reused
+    probe.close()
+    sizer = mf.MotionFocusEngine(max_streams=8, max_tick_frames=64, max_stream_frames=8,
+                                 device=dev)
+    base = sizer.stats().device_bytes                      # tables of this configuration
+    sizer.close()
+    budget = base + 2 * (1 << 20) + 2 * 128 * 100          # two 128-pose histories + reserves
+    eng = mf.MotionFocusEngine(max_streams=8, max_tick_frames=64, max_stream_frames=8,
+                               memory_budget=budget, device=dev)
+    eng.add_stream(64, 48, window=8, smooth_len=5, reserve_bytes=1 << 20)
+    eng.add_stream(64, 48, window=8, smooth_len=5, reserve_bytes=1 << 20)
+    with pytest.raises(mf.MFError) as e:
+        eng.add_stream(64, 48, window=8, smooth_len=5, reserve_bytes=1 << 20)
+    assert e.value.status == mf.MF_ERR_ADMISSION          # budget exhausted
+    st = eng.stats()
+    assert st.streams == 2 and st.accounted_bytes <= budget
+    eng.close()
+
+
+def test_engine_one_push_per_stream_per_tick(mf):
+    dev = torch.device("cuda", 0)
+    eng = mf.MotionFocusEngine(max_streams=2, max_tick_frames=64, max_stream_frames=8, device=dev)
+    s = eng.add_stream(64, 48, window=4, smooth_len=3)
+    P = _accelerating_walk(8)
+    M = torch.zeros((8, 48, 64), device=dev)
+    eng.submit(s, P[:4], None, (50.0, 50.0, 32.0, 24.0), M[:4])
+    with pytest.raises(mf.MFError) as e:
+        eng.submit(s, P[4:8], None, (50.0, 50.0, 32.0, 24.0), M[4:8])
+    assert e.value.status == mf.MF_ERR_NOT_READY
+    t = eng.tick()
+    eng.submit(s, P[4:8], None, (50.0, 50.0, 32.0, 24.0), M[4:8])
+    t2 = eng.tick()
+    eng.wait(t2)
+    assert eng.done(t) and eng.done(t2) and eng.tick() == -1
+    with pytest.raises(mf.MFError) as e:
+        eng.add_stream(63, 48)                             # odd width
+    assert e.value.status == mf.MF_ERR_INVALID_ARG
+    eng.close()
+
+
+def test_engine_batch_local_anchoring(mf):
+    world = walk(WalkerSpec(n_frames=60, seed=9, turns=True)).poses_w2c
+    rng = np.random.default_rng(4)
+    L, Ov = 16, 3
+    batches, start, b = [], 0, 0
+    while True:
+        hi = min(start + L, 60)
+        G = np.eye(4)
+        if b:
+            G[:3, :3] = rot_y(rng.uniform(-3, 3))
+            G[:3, 3] = rng.normal(size=3) * 5
+        batches.append(np.stack([(O.to4x4(world[k]) @ G)[:3] for k in range(start, hi)]))
+        if hi == 60:
+            break
+        start = hi - Ov
+        b += 1
+    dev = torch.device("cuda", 0)
+    eng = mf.MotionFocusEngine(max_streams=2, max_tick_frames=64, max_stream_frames=16, device=dev)
+    s = eng.add_stream(64, 48, window=8, smooth_len=5, mode="heading", pose_frame="batch_local",
+                       overlap=Ov)
+    M = torch.zeros((60, 48, 64), device=dev)
+    info = torch.zeros(60 * 64, dtype=torch.uint8, device=dev)
+    ref = O.OracleStream(O.Params(64, 48, window=8, smooth_len=5, mode=O.MODE_HEADING,
+                                  pose_frame=O.POSES_BATCH_LOCAL, overlap=Ov))
+    K = np.array([50.0, 50.0, 32.0, 24.0])
+    e0 = 0
+    for k, bt in enumerate(batches):
+        ne = len(bt) - (Ov if k else 0)
+        eng.submit(s, bt, None, K, M[e0:e0 + ne], None, info[e0 * 64:(e0 + ne) * 64])
+        t = eng.tick()
+        ref.push(bt, None, K)
+        e0 += ne
+    eng.wait(t)
+    assert e0 == 60
+    infos = info.cpu().numpy().view(mf.FRAME_INFO_DTYPE)
+    Mh = M.cpu().numpy()
+    intr = O.compensated_intrinsics(K, ref.p)
+    for n in range(60):
+        rinfo, rp, Mr, _ = ref.frame(n)
+        parity.check_frame(infos[n], None, rinfo, rp, intr, where=f"frame {n}")
+        parity.check_map(Mh[n], Mr, where=f"M {n}")
+    eng.close()
+
+
+def test_engine_tune_picks_a_candidate(mf):
+    dev = torch.device("cuda", 0)
+    eng = mf.MotionFocusEngine(max_streams=2, max_tick_frames=256, device=dev)
+    band = eng.tune(1920, 1080, 16)
+    assert 1 <= band <= 256 and (1080 + band - 1) // band * band >= 1080
+    eng.close()
