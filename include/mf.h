@@ -350,8 +350,65 @@ int mf_engine_tune(mf_engine* e, int32_t width, int32_t height, int32_t window, 
 
 int mf_engine_get_stats(mf_engine* e, mf_engine_stats* out);
 
+/* Per-frame latency of the ticks that have finished: from the frame's
+ * mf_engine_submit call to the GPU completing its tick (stamped by a host
+ * function enqueued behind the tick).  reset != 0 starts a new window. */
+typedef struct {
+  int64_t frames;   /* frames in the window */
+  double p50_ms, p90_ms, p99_ms, max_ms, mean_ms;
+} mf_latency_stats;
+
+int mf_engine_latency(mf_engine* e, mf_latency_stats* out, int32_t reset);
+
 /* Wait for all ticks and free everything. */
 int mf_engine_close(mf_engine* e);
+
+/* ---------------------------------------------------------------------------
+ * Serving loop: a thread-safe front end over an engine that batches frames
+ * as they arrive (continuous batching).  Clients admit streams, submit
+ * pushes from any thread and never call tick: a background thread launches
+ * a tick as soon as work is queued (after at most tick_us of gathering)
+ * while earlier ticks are still on the GPU (up to two in flight).  Pushes
+ * that arrive while a stream's previous push is waiting are queued per
+ * stream and go out in later ticks, in order.  Latency is measured from the
+ * client's mf_server_submit to the completion of the frame's tick on the GPU.
+ */
+typedef struct mf_server mf_server;
+
+typedef struct {
+  mf_engine_desc engine;   /* engine limits, dtypes, budget, flags, stream */
+  int32_t tick_us;         /* longest wait for more work before a tick (default 200) */
+  int32_t queue_limit;     /* queued pushes per stream before NOT_READY (default 64) */
+} mf_server_desc;
+
+void mf_server_desc_init(mf_server_desc* d);
+int mf_server_open(const mf_server_desc* d, mf_server** out);
+
+/* Admission as mf_engine_add_stream (MF_ERR_ADMISSION when no slot or no
+ * memory budget is left). */
+int mf_server_add_stream(mf_server* s, const mf_stream_desc* d, int64_t reserve_bytes,
+                         int32_t* slot);
+
+/* Queue one push (arguments as mf_engine_submit; poses are copied now).
+ * Thread-safe.  MF_ERR_NOT_READY when the stream's queue is full. */
+int mf_server_submit(mf_server* s, int32_t slot, int32_t n, const double* poses_w2c_3x4,
+                     const void* depth, const double* K, void* focus_map, void* guided_depth,
+                     mf_frame_info* info);
+
+/* Frames of the stream whose maps are complete on the GPU. */
+int mf_server_frames_done(mf_server* s, int32_t slot, int64_t* frames);
+
+/* Wait until every queued push of the stream is complete, then free its slot. */
+int mf_server_remove_stream(mf_server* s, int32_t slot);
+
+/* Wait until everything queued so far is complete (timeout_ns < 0: no bound). */
+int mf_server_drain(mf_server* s, int64_t timeout_ns);
+
+int mf_server_latency(mf_server* s, mf_latency_stats* out, int32_t reset);
+int mf_server_get_stats(mf_server* s, mf_engine_stats* out);
+
+/* Stop the thread, wait for the GPU, free everything. */
+int mf_server_close(mf_server* s);
 
 /* ---------------------------------------------------------------------------
  * Allocation-free rendering.  The paper has no counterpart to this entry

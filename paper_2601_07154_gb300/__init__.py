@@ -9,4 +9,4 @@ is its ctypes binding (``_mf``) plus a torch-facing wrapper (``stream``).
 """
 from . import _mf  # noqa: F401  (raises ImportError if libmf.so is missing)
 from ._mf import *  # noqa: F401,F403
-from .stream import MotionFocusEngine, MotionFocusStream  # noqa: F401
+from .stream import MotionFocusEngine, MotionFocusServer, MotionFocusStream  # noqa: F401

@@ -28,7 +28,10 @@ EXPORTED = ("mf_stream_desc_init", "mf_open_stream", "mf_push_frames", "mf_get_m
             "mf_last_error", "mf_render_noalloc", "mf_engine_desc_init", "mf_engine_open",
             "mf_engine_add_stream", "mf_engine_remove_stream", "mf_engine_submit",
             "mf_engine_tick", "mf_engine_query", "mf_engine_wait", "mf_engine_tune",
-            "mf_engine_get_stats", "mf_engine_close")
+            "mf_engine_get_stats", "mf_engine_close", "mf_engine_latency",
+            "mf_server_desc_init", "mf_server_open", "mf_server_add_stream", "mf_server_submit",
+            "mf_server_frames_done", "mf_server_remove_stream", "mf_server_drain",
+            "mf_server_latency", "mf_server_get_stats", "mf_server_close")
 MF_ENGINE_NO_GRAPH = 2
 MF_ENGINE_NO_TUNE = 4
 MF_NOALLOC_MAX_FRAMES = 256
@@ -80,6 +83,17 @@ class MFEngineStats(ctypes.Structure):
         ("device_bytes", ctypes.c_int64), ("accounted_bytes", ctypes.c_int64),
         ("tick_gpu_ms", ctypes.c_double),
     ]
+
+
+class MFLatencyStats(ctypes.Structure):
+    _fields_ = [("frames", ctypes.c_int64), ("p50_ms", ctypes.c_double),
+                ("p90_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("mean_ms", ctypes.c_double)]
+
+
+class MFServerDesc(ctypes.Structure):
+    _fields_ = [("engine", MFEngineDesc), ("tick_us", ctypes.c_int32),
+                ("queue_limit", ctypes.c_int32)]
 
 
 # numpy views of the C result records (layouts of include/mf.h)
@@ -139,12 +153,28 @@ def _load():
     lib.mf_engine_tune.argtypes = [vp, i32, i32, i32, ctypes.POINTER(i32)]
     lib.mf_engine_get_stats.argtypes = [vp, ctypes.POINTER(MFEngineStats)]
     lib.mf_engine_close.argtypes = [vp]
+    lib.mf_engine_latency.argtypes = [vp, ctypes.POINTER(MFLatencyStats), i32]
+    lib.mf_server_desc_init.argtypes = [ctypes.POINTER(MFServerDesc)]
+    lib.mf_server_desc_init.restype = None
+    lib.mf_server_open.argtypes = [ctypes.POINTER(MFServerDesc), ctypes.POINTER(vp)]
+    lib.mf_server_add_stream.argtypes = [vp, ctypes.POINTER(MFStreamDesc), i64,
+                                         ctypes.POINTER(i32)]
+    lib.mf_server_submit.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp]
+    lib.mf_server_frames_done.argtypes = [vp, i32, ctypes.POINTER(i64)]
+    lib.mf_server_remove_stream.argtypes = [vp, i32]
+    lib.mf_server_drain.argtypes = [vp, i64]
+    lib.mf_server_latency.argtypes = [vp, ctypes.POINTER(MFLatencyStats), i32]
+    lib.mf_server_get_stats.argtypes = [vp, ctypes.POINTER(MFEngineStats)]
+    lib.mf_server_close.argtypes = [vp]
     for name in ("mf_open_stream", "mf_push_frames", "mf_get_maps", "mf_sync",
                  "mf_pending_frames", "mf_reset_stream", "mf_stream_stats", "mf_close_stream",
                  "mf_render_noalloc", "mf_engine_open", "mf_engine_add_stream",
                  "mf_engine_remove_stream", "mf_engine_submit", "mf_engine_tick",
                  "mf_engine_query", "mf_engine_wait", "mf_engine_tune", "mf_engine_get_stats",
-                 "mf_engine_close"):
+                 "mf_engine_close", "mf_engine_latency", "mf_server_open",
+                 "mf_server_add_stream", "mf_server_submit", "mf_server_frames_done",
+                 "mf_server_remove_stream", "mf_server_drain", "mf_server_latency",
+                 "mf_server_get_stats", "mf_server_close"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -314,3 +344,70 @@ def mf_engine_get_stats(e):
 
 def mf_engine_close(e):
     _check(lib.mf_engine_close(e), "mf_engine_close")
+
+
+def mf_engine_latency(e, reset=False):
+    st = MFLatencyStats()
+    _check(lib.mf_engine_latency(e, ctypes.byref(st), 1 if reset else 0), "mf_engine_latency")
+    return st
+
+
+# ----------------------------------------------------------- server --------
+def mf_server_desc_init(engine=None, **fields):
+    d = MFServerDesc()
+    lib.mf_server_desc_init(ctypes.byref(d))
+    if engine is not None:
+        d.engine = engine
+    for k, v in fields.items():
+        if not hasattr(d, k):
+            raise TypeError(f"unknown server field {k}")
+        setattr(d, k, v)
+    return d
+
+
+def mf_server_open(desc):
+    h = ctypes.c_void_p()
+    _check(lib.mf_server_open(ctypes.byref(desc), ctypes.byref(h)), "mf_server_open")
+    return h.value
+
+
+def mf_server_add_stream(s, stream_desc, reserve_bytes=0):
+    slot = ctypes.c_int32()
+    _check(lib.mf_server_add_stream(s, ctypes.byref(stream_desc), int(reserve_bytes),
+                                    ctypes.byref(slot)), "mf_server_add_stream")
+    return slot.value
+
+
+def mf_server_submit(s, slot, n, poses, depth, K, focus_map=None, guided_depth=None, info=None):
+    _check(lib.mf_server_submit(s, int(slot), int(n), ptr(poses), ptr(depth), ptr(K),
+                                ptr(focus_map), ptr(guided_depth), ptr(info)), "mf_server_submit")
+
+
+def mf_server_frames_done(s, slot):
+    n = ctypes.c_int64()
+    _check(lib.mf_server_frames_done(s, int(slot), ctypes.byref(n)), "mf_server_frames_done")
+    return n.value
+
+
+def mf_server_remove_stream(s, slot):
+    _check(lib.mf_server_remove_stream(s, int(slot)), "mf_server_remove_stream")
+
+
+def mf_server_drain(s, timeout_ns=-1):
+    _check(lib.mf_server_drain(s, int(timeout_ns)), "mf_server_drain")
+
+
+def mf_server_latency(s, reset=False):
+    st = MFLatencyStats()
+    _check(lib.mf_server_latency(s, ctypes.byref(st), 1 if reset else 0), "mf_server_latency")
+    return st
+
+
+def mf_server_get_stats(s):
+    st = MFEngineStats()
+    _check(lib.mf_server_get_stats(s, ctypes.byref(st)), "mf_server_get_stats")
+    return st
+
+
+def mf_server_close(s):
+    _check(lib.mf_server_close(s), "mf_server_close")

@@ -5,7 +5,10 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <deque>
+#include <memory>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -67,6 +70,33 @@ int default_band(int height) {
   return (height + bands - 1) / bands;
 }
 
+}  // namespace
+
+int64_t mf::engine_now_ns() {
+  return std::chrono::duration_cast<std::chrono::nanoseconds>(
+             std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+namespace {
+
+int64_t now_ns() {
+  return std::chrono::duration_cast<std::chrono::nanoseconds>(
+             std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+// Submit times of one tick's frames and the time its work finished on the
+// GPU (written by a host function the driver runs behind the tick).
+struct TickRecord {
+  std::vector<int64_t> submit_ns;  // one per frame
+  std::atomic<int64_t> done_ns{0};
+};
+
+void CUDART_CB stamp_tick_done(void* p) {
+  static_cast<TickRecord*>(p)->done_ns.store(now_ns(), std::memory_order_release);
+}
+
 struct Slot {
   bool used = false;
   mf_stream_desc d{};
@@ -112,6 +142,10 @@ struct mf_engine {
   int64_t device_bytes = 0;
   double tick_ms = 0.0;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending_timers;
+  // latency accounting
+  std::vector<int64_t> frame_submit_ns;          // the tick being assembled
+  std::deque<std::unique_ptr<TickRecord>> in_flight;
+  std::vector<double> latencies_ms;
 
   void* dalloc(size_t n) {
     void* p = nullptr;
@@ -409,6 +443,17 @@ int tune_class(mf_engine* e, int width, int height, int window, int* band_out) {
   return MF_OK;
 }
 
+// Moves the latencies of finished ticks (in order) into the window.
+void collect_latencies(mf_engine* e) {
+  while (!e->in_flight.empty()) {
+    TickRecord* r = e->in_flight.front().get();
+    const int64_t done = r->done_ns.load(std::memory_order_acquire);
+    if (!done) break;
+    for (int64_t t : r->submit_ns) e->latencies_ms.push_back((double)(done - t) * 1e-6);
+    e->in_flight.pop_front();
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -572,6 +617,14 @@ int mf_engine_remove_stream(mf_engine* e, int32_t slot) {
 
 int mf_engine_submit(mf_engine* e, int32_t slot, int32_t n, const double* poses, const void* depth,
                      const double* K, void* focus_map, void* guided_depth, mf_frame_info* info) {
+  return mf::engine_submit_at(e, slot, n, poses, depth, K, focus_map, guided_depth, info, now_ns());
+}
+
+}  // extern "C"
+
+int mf::engine_submit_at(mf_engine* e, int32_t slot, int32_t n, const double* poses,
+                         const void* depth, const double* K, void* focus_map, void* guided_depth,
+                         mf_frame_info* info, int64_t t_sub) {
   if (!e || slot < 0 || slot >= e->d.max_streams || !e->slots[slot].used)
     return fail(MF_ERR_INVALID_ARG, "no such stream");
   Slot& s = e->slots[slot];
@@ -622,12 +675,15 @@ int mf_engine_submit(mf_engine* e, int32_t slot, int32_t n, const double* poses,
     t.info = info ? info + k : nullptr;
     e->frames.push_back(t);
   }
+  e->frame_submit_ns.insert(e->frame_submit_ns.end(), (size_t)n_emit, t_sub);
   s.emitted += n_emit;
   ++s.pushes;
   s.pending_tick = e->next_tick;
   s.last_tick = e->next_tick;
   return MF_OK;
 }
+
+extern "C" {
 
 int mf_engine_tick(mf_engine* e, int64_t* tick) {
   if (!e || !tick) return fail(MF_ERR_INVALID_ARG, "NULL argument");
@@ -668,6 +724,13 @@ int mf_engine_tick(mf_engine* e, int64_t* tick) {
     e->pending_timers.emplace_back(ta, tb);
   }
   ENG_CUDA(cudaEventRecord(e->done[b], e->st), "event");
+  {
+    std::unique_ptr<TickRecord> rec(new TickRecord());
+    rec->submit_ns.swap(e->frame_submit_ns);
+    ENG_CUDA(cudaLaunchHostFunc(e->st, stamp_tick_done, rec.get()), "tick completion stamp");
+    e->in_flight.push_back(std::move(rec));
+  }
+  e->frame_submit_ns.clear();
   e->buf_tick[b] = t;
   ++e->ticks;
   e->frames_done += (int64_t)e->frames.size();
@@ -729,6 +792,31 @@ int mf_engine_get_stats(mf_engine* e, mf_engine_stats* out) {
   out->device_bytes = e->device_bytes;
   out->accounted_bytes = e->accounted();
   out->tick_gpu_ms = e->tick_ms;
+  return MF_OK;
+}
+
+int mf_engine_latency(mf_engine* e, mf_latency_stats* out, int32_t reset) {
+  if (!e || !out) return fail(MF_ERR_INVALID_ARG, "NULL argument");
+  collect_latencies(e);
+  std::memset(out, 0, sizeof(*out));
+  std::vector<double>& v = e->latencies_ms;
+  out->frames = (int64_t)v.size();
+  if (!v.empty()) {
+    std::vector<double> s(v);
+    std::sort(s.begin(), s.end());
+    auto q = [&](double p) {
+      const size_t i = std::min(s.size() - 1, (size_t)std::ceil(p * s.size()) - (p > 0 ? 1 : 0));
+      return s[i];
+    };
+    out->p50_ms = q(0.50);
+    out->p90_ms = q(0.90);
+    out->p99_ms = q(0.99);
+    out->max_ms = s.back();
+    double sum = 0.0;
+    for (double x : s) sum += x;
+    out->mean_ms = sum / s.size();
+  }
+  if (reset) v.clear();
   return MF_OK;
 }
 

@@ -71,4 +71,11 @@ size_t engine_map_smem();
 cudaError_t launch_engine_map_only(const EngineKernelArgs& a, int depth_dtype, int map_dtype,
                                    int map_grid, cudaStream_t st);
 
+// mf_engine_submit with an explicit submit time (steady-clock ns) for the
+// latency statistics; the serving loop passes its clients' submit times.
+int engine_submit_at(mf_engine* e, int32_t slot, int32_t n, const double* poses, const void* depth,
+                     const double* K, void* focus_map, void* guided_depth, mf_frame_info* info,
+                     int64_t submit_ns);
+int64_t engine_now_ns();
+
 }  // namespace mf

@@ -209,10 +209,83 @@ class MotionFocusEngine:
     def stats(self):
         return _mf.mf_engine_get_stats(self.handle)
 
+    def latency(self, reset=False):
+        """Per-frame submit-to-completion latency (ms) of the finished ticks."""
+        return _mf.mf_engine_latency(self.handle, reset)
+
     def close(self):
         if getattr(self, "handle", None):
             with torch.cuda.device(self.device):
                 _mf.mf_engine_close(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class MotionFocusServer:
+    """Continuous batching over an engine (the C ABI's mf_server_*).
+
+    Streams are admitted with ``add_stream``; ``submit`` queues a push from
+    any thread and returns at once; a native thread batches queued pushes of
+    all streams into ticks while earlier ticks run on the GPU.
+    """
+
+    def __init__(self, max_streams=256, max_tick_frames=4096, max_stream_frames=64,
+                 depth_dtype=torch.float32, map_dtype=torch.float32, memory_budget=0,
+                 tick_us=200, queue_limit=64, graph=True, tune=True, device=None):
+        self.device = torch.device(device) if device is not None else torch.device(
+            "cuda", torch.cuda.current_device())
+        self.depth_dtype, self.map_dtype = depth_dtype, map_dtype
+        flags = (0 if graph else _mf.MF_ENGINE_NO_GRAPH) | (0 if tune else _mf.MF_ENGINE_NO_TUNE)
+        eng = _mf.mf_engine_desc_init(
+            max_streams=max_streams, max_tick_frames=max_tick_frames,
+            max_stream_frames=max_stream_frames, depth_dtype=_DT[depth_dtype],
+            map_dtype=_DT[map_dtype], flags=flags, memory_budget=int(memory_budget))
+        self.desc = _mf.mf_server_desc_init(engine=eng, tick_us=int(tick_us),
+                                            queue_limit=int(queue_limit))
+        with torch.cuda.device(self.device):
+            self.handle = _mf.mf_server_open(self.desc)
+
+    def add_stream(self, width, height, window=8, smooth_len=15, mode="accel",
+                   pose_frame="world", overlap=0, calib=None, reserve_bytes=0):
+        cw, ch = calib if calib is not None else (0, 0)
+        d = _mf.mf_stream_desc_init(
+            width=int(width), height=int(height), calib_width=cw, calib_height=ch,
+            window=int(window), smooth_len=int(smooth_len), mode=_MODES[mode],
+            pose_frame=_FRAMES[pose_frame], overlap=int(overlap),
+            depth_dtype=_DT[self.depth_dtype], map_dtype=_DT[self.map_dtype])
+        with torch.cuda.device(self.device):
+            return _mf.mf_server_add_stream(self.handle, d, reserve_bytes)
+
+    def submit(self, slot, poses, depth, K, focus_map=None, guided_depth=None, info=None):
+        P = np.ascontiguousarray(np.asarray(poses, dtype=np.float64))
+        Kh = np.ascontiguousarray(np.asarray(K, dtype=np.float64).reshape(4))
+        _mf.mf_server_submit(self.handle, slot, P.shape[0], P, depth, Kh, focus_map,
+                             guided_depth, info)
+
+    def frames_done(self, slot):
+        return _mf.mf_server_frames_done(self.handle, slot)
+
+    def remove_stream(self, slot):
+        _mf.mf_server_remove_stream(self.handle, slot)
+
+    def drain(self, timeout_ns=-1):
+        _mf.mf_server_drain(self.handle, timeout_ns)
+
+    def latency(self, reset=False):
+        return _mf.mf_server_latency(self.handle, reset)
+
+    def stats(self):
+        return _mf.mf_server_get_stats(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            with torch.cuda.device(self.device):
+                _mf.mf_server_close(self.handle)
             self.handle = None
 
     def __del__(self):
