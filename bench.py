@@ -19,6 +19,7 @@ product path) on the host cores on a bounded sample of the same workload.
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -226,9 +227,29 @@ def run_gpu(args):
     prec = None
     if rank == 0 and not args.no_precision:
         prec = run_precision(torch, mf, w, poses, depth, dev, args, value / world)
+    batched = served = None
+    if rank == 0 and not args.no_serving:
+        del M, G
+        M = G = None
+        pools32 = depth_pools(torch, dev, args.batch_frames, torch.float32)
+        pools16 = {k: v.to(torch.bfloat16) for k, v in pools32.items()}
+        batched = {"workload": "64 streams, resolutions 640x480..3840x2160, windows 8..32, "
+                               f"{args.batch_frames} frames per stream per step",
+                   "engine_f32": run_batched(torch, mf, dev, args, pools32, torch.float32),
+                   "engine_bf16": run_batched(torch, mf, dev, args, pools16, torch.bfloat16),
+                   "plain_f32": run_batched(torch, mf, dev, args, pools32, torch.float32, plain=True)}
+        for k in ("engine_f32", "engine_bf16"):
+            batched[k]["vs_plain_f32"] = round(batched[k]["value"] / batched["plain_f32"]["value"], 3)
+        served = {"workload": "Poisson arrivals 4/s of 30 fps streams (mean 32 s), 128 live at "
+                              "start, cap 256, mixed resolutions, admission by memory budget "
+                              f"{args.serve_budget_gb} GB",
+                  "server_bf16": run_served(torch, mf, dev, args, pools16, torch.bfloat16),
+                  "server_f32": run_served(torch, mf, dev, args, pools32, torch.float32),
+                  "plain_f32": run_served(torch, mf, dev, args, pools32, torch.float32, plain=True)}
+        del pools32, pools16
     e2e = None
     if rank == 0 and not args.no_e2e:
-        del M, G
+        M = G = None
         e2e = run_e2e(torch, mf, w, depth, dev, args)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -251,7 +272,7 @@ def run_gpu(args):
                          "algorithmic_bytes_per_launch": frames * FRAME_BYTES,
                          "launch_ms": round(map_ms, 4)},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
-            "precision": prec,
+            "precision": prec, "batched": batched, "served": served,
         }
         print(json.dumps(rec), flush=True)
     if world > 1:
@@ -334,6 +355,267 @@ def run_e2e(torch, mf, w, depth_dev, dev, args):
             "d2h_bytes_per_step": 2 * FR * WIDTH * HEIGHT * 4 + FR * 64}
 
 
+# ------------------------------------------------- batched and served --
+MIX_RES = ((640, 480), (1280, 720), (1920, 1080), (3840, 2160))
+
+
+def depth_pools(torch, dev, planes, dtype):
+    """Per-resolution pools of ray-cast depth planes, shared read-only inputs."""
+    from synth import hd_stream
+    from synth.scene import render_depth
+    w = hd_stream()
+    pools = {}
+    for width, height in MIX_RES:
+        f = 0.9 * width
+        intr = (f, f, width / 2.0, height / 2.0)
+        imgs = [render_depth(w.boxes, w.traj.rot_c2w[(37 * k) % FRAMES],
+                             w.traj.centres[(37 * k) % FRAMES], intr, width, height)
+                for k in range(planes)]
+        pools[(width, height)] = torch.from_numpy(np.stack(imgs)).to(dev).to(dtype)
+    return pools
+
+
+def run_batched(torch, mf, dev, args, pools, dtype, plain=False):
+    """64 mixed streams (640x480 .. 3840x2160, windows 8..32): every step
+    pushes F frames of every stream; engine ticks or plain per-stream calls."""
+    from synth import mixed_streams
+    F, n_streams = args.batch_frames, 64
+    specs = mixed_streams(n_streams, cfg=4)
+    steps, warm = args.batch_steps, 3
+    need = (steps + warm) * F
+    st = torch.cuda.Stream(dev)
+    streams = []
+    for sp in specs:
+        P = sp.poses
+        idx = np.arange(need) % len(P)
+        streams.append(dict(
+            w=sp.width, h=sp.height, win=sp.window, K=np.ascontiguousarray(sp.K()),
+            poses=np.ascontiguousarray(P[idx]),
+            M=torch.empty((F, sp.height, sp.width), dtype=dtype, device=dev),
+            G=torch.empty((F, sp.height, sp.width), dtype=dtype, device=dev),
+            info=torch.empty(F * 64, dtype=torch.uint8, device=dev),
+            depth=pools[(sp.width, sp.height)][:F]))
+    px = sum(s["w"] * s["h"] for s in streams) * F
+    bpp = 3 * (4 if dtype == torch.float32 else 2)
+    if plain:
+        handles = []
+        for s in streams:
+            h = mf.MotionFocusStream(s["w"], s["h"], window=s["win"], smooth_len=SMOOTH, device=dev,
+                                     cuda_stream=st, depth_dtype=dtype, map_dtype=dtype,
+                                     max_pending=F)
+            s["poses_dev"] = torch.from_numpy(s["poses"]).to(dev)
+            handles.append(h)
+
+        def step(k):
+            for h, s in zip(handles, streams):
+                mf.mf_push_frames(h.handle, F, s["poses_dev"][k * F:(k + 1) * F], s["depth"], s["K"])
+                mf.mf_get_maps(h.handle, F, s["M"], s["G"], s["info"], None)
+    else:
+        eng = mf.MotionFocusEngine(max_streams=n_streams, max_tick_frames=n_streams * F,
+                                   max_stream_frames=F, depth_dtype=dtype, map_dtype=dtype,
+                                   device=dev, cuda_stream=st)
+        slots = [eng.add_stream(s["w"], s["h"], window=s["win"], smooth_len=SMOOTH) for s in streams]
+        rec = np.zeros(n_streams, dtype=mf.PUSH_DTYPE)
+        rec["slot"] = slots
+        rec["n"] = F
+        rec["depth"] = [s["depth"].data_ptr() for s in streams]
+        rec["K"] = [s["K"].ctypes.data for s in streams]
+        rec["focus_map"] = [s["M"].data_ptr() for s in streams]
+        rec["guided_depth"] = [s["G"].data_ptr() for s in streams]
+        rec["info"] = [s["info"].data_ptr() for s in streams]
+        pose_base = np.array([s["poses"].ctypes.data for s in streams], dtype=np.uint64)
+
+        def step(k):
+            rec["poses"] = pose_base + np.uint64(k * F * 96)
+            mf.mf_engine_submit_batch(eng.handle, rec)
+            eng.tick()
+    for k in range(warm):
+        step(k)
+    st.synchronize()
+    l0 = mf.mf_total_kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    ev0.record(st)
+    for k in range(warm, warm + steps):
+        step(k)
+    ev1.record(st)
+    ev1.synchronize()
+    wall = time.perf_counter() - t0
+    ms = ev0.elapsed_time(ev1)
+    launches = mf.mf_total_kernel_launches() - l0
+    frames = n_streams * F * steps
+    out = {"value": round(frames / (ms / 1000.0), 1), "unit": "frames/s",
+           "mpx_per_s": round(px * steps / (ms / 1000.0) / 1e6, 1),
+           "hbm_gbs": round(px * steps * bpp / (ms / 1000.0) / 1e9, 1),
+           "ms_per_step": round(ms / steps, 3), "host_ms_per_step": round(1000 * wall / steps, 3),
+           "frames_per_step": n_streams * F, "steps": steps, "kernel_launches_per_step": launches / steps}
+    if not plain:
+        est = eng.stats()
+        out["graph_launches"] = int(est.graph_launches)
+        eng.close()
+    return out
+
+
+def run_served(torch, mf, dev, args, pools, dtype, plain=False):
+    """Poisson arrivals (4/s) of 30 fps streams (mean 32 s, resolutions of the
+    mixed workload), 128 live at the start, up to 256; admission by memory.
+
+    Every frame arrives on its stream's 30 fps schedule; latency runs from
+    that arrival time to the GPU completion of the frame (native stamp for
+    the server; host-observed event for the plain per-stream path).  The
+    expected resolution classes are tuned and the first 128 streams admitted
+    before the clock starts, as a deployment would warm up.
+    """
+    from synth import Xoshiro256ss, WalkerSpec, walk
+    rng = Xoshiro256ss(5150)
+    duration = args.serve_seconds if not plain else min(args.serve_seconds, 6.0)
+    trajs = [np.ascontiguousarray(walk(WalkerSpec(n_frames=900, seed=5100 + i, turns=True)).poses_w2c)
+             for i in range(8)]
+    R = 8
+    esize = 4 if dtype == torch.float32 else 2
+    budget = int(args.serve_budget_gb * 2 ** 30)
+    st = torch.cuda.Stream(dev)
+    if not plain:
+        srv = mf.MotionFocusServer(max_streams=256, max_tick_frames=1024, max_stream_frames=4,
+                                   depth_dtype=dtype, map_dtype=dtype, memory_budget=budget,
+                                   tick_us=args.tick_us, device=dev)
+        for width, height in MIX_RES:
+            for win in (8, 16, 32):
+                srv.tune(width, height, win)
+    rings = {}   # resolution -> free (M, G) output rings of the clients
+
+    def new_stream(t_start):
+        width, height = rng.choice(MIX_RES)
+        win = int(rng.uniform(8, 33))
+        length = max(30, int(-math.log(1.0 - rng.uniform()) * 32.0 * 30))
+        f = rng.uniform(0.7, 1.2) * width
+        return dict(w=width, h=height, win=win, length=length,
+                    K=np.ascontiguousarray([f, f, width / 2, height / 2], dtype=np.float64),
+                    traj=trajs[int(rng.uniform(0, len(trajs)))], off=int(rng.uniform(0, 900)),
+                    t0=t_start, sent=0)
+
+    counters = {"refused": 0, "admitted": 0}
+
+    def admit(s, now):
+        plane = s["w"] * s["h"] * esize
+        try:
+            if plain:
+                s["handle"] = mf.MotionFocusStream(s["w"], s["h"], window=s["win"], smooth_len=SMOOTH,
+                                                   device=dev, cuda_stream=st, depth_dtype=dtype,
+                                                   map_dtype=dtype, max_pending=R)
+            else:
+                s["slot"] = srv.add_stream(s["w"], s["h"], window=s["win"], smooth_len=SMOOTH,
+                                           reserve_bytes=2 * R * plane)
+        except mf.MFError as e:
+            if e.status == mf.MF_ERR_ADMISSION:
+                counters["refused"] += 1
+                return False
+            raise
+        free = rings.setdefault((s["w"], s["h"]), [])
+        if free:
+            s["M"], s["G"] = free.pop()
+        else:
+            s["M"] = torch.empty((R, s["h"], s["w"]), dtype=dtype, device=dev)
+            s["G"] = torch.empty_like(s["M"])
+        s["plane"] = plane
+        s["pool"] = pools[(s["w"], s["h"])]
+        s["t0"] = max(s["t0"], now)
+        counters["admitted"] += 1
+        return True
+
+    def retire(s):
+        if plain:
+            s["handle"].close()
+        else:
+            srv.remove_stream(s["slot"])
+        rings[(s["w"], s["h"])].append((s["M"], s["G"]))
+
+    active = [s for s in (new_stream(0.0) for _ in range(128)) if admit(s, 0.0)]
+    waiting, lags, lat_plain, pending_events, done = [], [], [], [], []
+    torch.cuda.synchronize(dev)
+    next_arrival = -math.log(1.0 - rng.uniform()) / 4.0
+    served = 0
+    t0_ns = mf.mf_clock_ns()
+    t_begin = time.perf_counter()
+    while True:
+        now = time.perf_counter() - t_begin
+        if now >= duration:
+            break
+        while next_arrival <= now:
+            waiting.append(new_stream(next_arrival))
+            next_arrival += -math.log(1.0 - rng.uniform()) / 4.0
+        if waiting:
+            still = []
+            for s in waiting:
+                if len(active) < 256 and admit(s, now):
+                    active.append(s)
+                else:
+                    still.append(s)
+            waiting = still
+        keep, batch = [], []
+        for s in active:
+            due = min(s["length"], int((now - s["t0"]) * 30.0) + 1)
+            while s["sent"] < due:
+                k = s["sent"]
+                r = k % R
+                pk = (s["off"] + k) % 900
+                if plain:
+                    mf.mf_push_frames(s["handle"].handle, 1, s["traj"][pk][None], s["pool"][r], s["K"])
+                    mf.mf_get_maps(s["handle"].handle, 1, s["M"][r], s["G"][r], None, None)
+                    ev = torch.cuda.Event()
+                    ev.record(st)
+                    pending_events.append((ev, s["t0"] + k / 30.0))
+                else:
+                    batch.append((s["slot"], 1, s["traj"].ctypes.data + pk * 96,
+                                  s["pool"].data_ptr() + r * s["plane"], s["K"].ctypes.data,
+                                  s["M"].data_ptr() + r * s["plane"], s["G"].data_ptr() + r * s["plane"],
+                                  0, t0_ns + int((s["t0"] + k / 30.0) * 1e9)))
+                lags.append(now - (s["t0"] + k / 30.0))
+                s["sent"] += 1
+                served += 1
+            (done if s["sent"] >= s["length"] else keep).append(s)
+        active = keep
+        if batch:
+            mf.mf_server_submit_batch(srv.handle, np.array(batch, dtype=mf.PUSH_DTYPE))
+        for s in done:
+            retire(s)
+        done.clear()
+        if plain:
+            while pending_events and pending_events[0][0].query():
+                ev, due_t = pending_events.pop(0)
+                lat_plain.append(1000.0 * (time.perf_counter() - t_begin - due_t))
+    if plain:
+        st.synchronize()
+        for ev, due_t in pending_events:
+            lat_plain.append(1000.0 * (time.perf_counter() - t_begin - due_t))
+        lat = np.array(lat_plain)
+        out = {"p50_ms": round(float(np.percentile(lat, 50)), 3),
+               "p90_ms": round(float(np.percentile(lat, 90)), 3),
+               "p99_ms": round(float(np.percentile(lat, 99)), 3),
+               "max_ms": round(float(lat.max()), 3),
+               "latency": "frame arrival (30 fps schedule) -> completion observed by the host"}
+        for s in active:
+            s["handle"].close()
+    else:
+        srv.drain()
+        lat = srv.latency()
+        est = srv.stats()
+        out = {"p50_ms": round(lat.p50_ms, 3), "p90_ms": round(lat.p90_ms, 3),
+               "p99_ms": round(lat.p99_ms, 3), "max_ms": round(lat.max_ms, 3),
+               "latency": "frame arrival (30 fps schedule) -> GPU completion of its tick (native)",
+               "ticks": int(est.ticks), "frames_per_tick": round(est.frames / max(1, est.ticks), 2)}
+        for s in active:
+            srv.remove_stream(s["slot"])
+        srv.close()
+    wall = time.perf_counter() - t_begin
+    lagv = np.array(lags) * 1000.0
+    out.update({"frames": served, "seconds": round(wall, 2), "value": round(served / wall, 1),
+                "unit": "frames/s", "admitted": counters["admitted"],
+                "refused_admissions": counters["refused"], "live_streams_end": len(active),
+                "submit_lag_p99_ms": round(float(np.percentile(lagv, 99)), 3)})
+    return out
+
+
 # ------------------------------------------------------------- CPU oracle --
 def oracle_sample(w, frames, rows):
     """Oracle frames/s on frames (full pose path) x rows of their maps."""
@@ -411,6 +693,12 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--batch-frames", type=int, default=8)
+    ap.add_argument("--batch-steps", type=int, default=20)
+    ap.add_argument("--serve-seconds", type=float, default=12.0)
+    ap.add_argument("--serve-budget-gb", type=float, default=32.0)
+    ap.add_argument("--tick-us", type=int, default=200)
     ap.add_argument("--frames", type=int, default=FRAMES,
                     help="frames per step (default: the full 900-frame workload; "
                          "smaller values only for profiling captures)")

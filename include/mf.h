@@ -305,13 +305,16 @@ void mf_engine_desc_init(mf_engine_desc* d);
 int mf_engine_open(const mf_engine_desc* d, mf_engine** out);
 
 /* Admit a stream described by *d (its dtypes must equal the engine's, its
- * width must be even; its cuda_stream and allocator fields are ignored).  The stream's pose history
- * is allocated on the device and stays resident until removal.
+ * width must be even; its cuda_stream and allocator fields are ignored).
+ * The stream's pose history (preallocated for every slot at open) stays
+ * resident on the device until removal; admission allocates nothing and does
+ * not wait, unless it must first tune a new resolution class (the
+ * autotuner runs synchronously; mf_engine_tune can run it beforehand).
  * reserve_bytes: device memory the caller will hold for this stream (its
- * output planes, say), counted with the history against memory_budget.
- * On success *slot names the stream.  MF_ERR_ADMISSION when every slot is
- * taken or the budget would be exceeded; MF_ERR_INVALID_ARG for a bad
- * descriptor.  May run the autotuner for a new resolution class. */
+ * output planes, say), counted with the engine's own memory against
+ * memory_budget.  On success *slot names the stream.  MF_ERR_ADMISSION when
+ * every slot is taken or the budget would be exceeded; MF_ERR_INVALID_ARG for
+ * a bad descriptor. */
 int mf_engine_add_stream(mf_engine* e, const mf_stream_desc* d, int64_t reserve_bytes,
                          int32_t* slot);
 
@@ -333,6 +336,26 @@ int mf_engine_submit(mf_engine* e, int32_t slot, int32_t n, const double* poses_
                      const void* depth, const double* K, void* focus_map, void* guided_depth,
                      mf_frame_info* info);
 
+/* One push for the batched submit calls below (64 bytes). */
+typedef struct {
+  int32_t slot, n;              /* stream and pose count, as mf_engine_submit */
+  const double* poses_w2c_3x4;  /* host, n x 12 FP64 */
+  const void* depth;            /* device planes or NULL */
+  const double* K;              /* host, fx fy cx cy */
+  void* focus_map;              /* device planes or NULL */
+  void* guided_depth;           /* device planes or NULL */
+  mf_frame_info* info;          /* device records or NULL */
+  int64_t arrival_ns;           /* when the frames arrived, on mf_clock_ns()'s clock;
+                                   0 = now.  Latency statistics start here. */
+} mf_push;
+
+/* The monotonic clock (nanoseconds) of arrival times and latency statistics. */
+int64_t mf_clock_ns(void);
+
+/* mf_engine_submit for n pushes in order; *accepted receives how many were
+ * queued.  Stops at the first push that fails and returns its status. */
+int mf_engine_submit_batch(mf_engine* e, int32_t n, const mf_push* pushes, int32_t* accepted);
+
 /* Launch everything submitted since the previous tick as one batch.  Does
  * not wait.  *tick receives its id (-1 if nothing was submitted). */
 int mf_engine_tick(mf_engine* e, int64_t* tick);
@@ -343,9 +366,10 @@ int mf_engine_query(mf_engine* e, int64_t tick, int32_t* done);
 /* Wait for tick `tick` (bounded by timeout_ns; < 0 = no bound). */
 int mf_engine_wait(mf_engine* e, int64_t tick, int64_t timeout_ns);
 
-/* Time the map kernel on a synthetic batch of width x height frames with a
- * window of `window` points for each candidate tile height and keep the
- * fastest for that resolution class; *band_h receives it.  Synchronous. */
+/* Time the map kernel on a synthetic batch of width x height frames whose
+ * points all reach the frame, with the window rounded up to 8, 16 or 32
+ * points, for each candidate tile height, and keep the fastest for that
+ * class (resolution, window bucket); *band_h receives it.  Synchronous. */
 int mf_engine_tune(mf_engine* e, int32_t width, int32_t height, int32_t window, int32_t* band_h);
 
 int mf_engine_get_stats(mf_engine* e, mf_engine_stats* out);
@@ -395,6 +419,11 @@ int mf_server_submit(mf_server* s, int32_t slot, int32_t n, const double* poses_
                      const void* depth, const double* K, void* focus_map, void* guided_depth,
                      mf_frame_info* info);
 
+/* mf_server_submit for n pushes under one lock; *accepted as in
+ * mf_engine_submit_batch.  Latency statistics start at each push's
+ * arrival_ns (0: the call's time). */
+int mf_server_submit_batch(mf_server* s, int32_t n, const mf_push* pushes, int32_t* accepted);
+
 /* Frames of the stream whose maps are complete on the GPU. */
 int mf_server_frames_done(mf_server* s, int32_t slot, int64_t* frames);
 
@@ -406,6 +435,10 @@ int mf_server_drain(mf_server* s, int64_t timeout_ns);
 
 int mf_server_latency(mf_server* s, mf_latency_stats* out, int32_t reset);
 int mf_server_get_stats(mf_server* s, mf_engine_stats* out);
+
+/* mf_engine_tune on the server's engine (tune expected classes before
+ * serving: tuning a new class at admission stalls the loop meanwhile). */
+int mf_server_tune(mf_server* s, int32_t width, int32_t height, int32_t window, int32_t* band_h);
 
 /* Stop the thread, wait for the GPU, free everything. */
 int mf_server_close(mf_server* s);

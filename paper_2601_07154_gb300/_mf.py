@@ -31,7 +31,8 @@ EXPORTED = ("mf_stream_desc_init", "mf_open_stream", "mf_push_frames", "mf_get_m
             "mf_engine_get_stats", "mf_engine_close", "mf_engine_latency",
             "mf_server_desc_init", "mf_server_open", "mf_server_add_stream", "mf_server_submit",
             "mf_server_frames_done", "mf_server_remove_stream", "mf_server_drain",
-            "mf_server_latency", "mf_server_get_stats", "mf_server_close")
+            "mf_server_latency", "mf_server_get_stats", "mf_server_close", "mf_clock_ns",
+            "mf_engine_submit_batch", "mf_server_submit_batch", "mf_server_tune")
 MF_ENGINE_NO_GRAPH = 2
 MF_ENGINE_NO_TUNE = 4
 MF_NOALLOC_MAX_FRAMES = 256
@@ -104,7 +105,11 @@ FRAME_INFO_DTYPE = np.dtype([
     ("reserved", "<i4")])
 MOTION_POINT_DTYPE = np.dtype([("u", "<f8"), ("v", "<f8"), ("sigma", "<f8"), ("s", "<f8"),
                                ("valid", "<i4"), ("reserved", "<i4")])
+PUSH_DTYPE = np.dtype([("slot", "<i4"), ("n", "<i4"), ("poses", "<u8"), ("depth", "<u8"),
+                       ("K", "<u8"), ("focus_map", "<u8"), ("guided_depth", "<u8"),
+                       ("info", "<u8"), ("arrival_ns", "<i8")])
 assert FRAME_INFO_DTYPE.itemsize == 64 and MOTION_POINT_DTYPE.itemsize == 40
+assert PUSH_DTYPE.itemsize == 64
 
 
 class MFError(RuntimeError):
@@ -166,6 +171,10 @@ def _load():
     lib.mf_server_latency.argtypes = [vp, ctypes.POINTER(MFLatencyStats), i32]
     lib.mf_server_get_stats.argtypes = [vp, ctypes.POINTER(MFEngineStats)]
     lib.mf_server_close.argtypes = [vp]
+    lib.mf_clock_ns.restype = i64
+    lib.mf_engine_submit_batch.argtypes = [vp, i32, vp, ctypes.POINTER(i32)]
+    lib.mf_server_submit_batch.argtypes = [vp, i32, vp, ctypes.POINTER(i32)]
+    lib.mf_server_tune.argtypes = [vp, i32, i32, i32, ctypes.POINTER(i32)]
     for name in ("mf_open_stream", "mf_push_frames", "mf_get_maps", "mf_sync",
                  "mf_pending_frames", "mf_reset_stream", "mf_stream_stats", "mf_close_stream",
                  "mf_render_noalloc", "mf_engine_open", "mf_engine_add_stream",
@@ -174,7 +183,8 @@ def _load():
                  "mf_engine_close", "mf_engine_latency", "mf_server_open",
                  "mf_server_add_stream", "mf_server_submit", "mf_server_frames_done",
                  "mf_server_remove_stream", "mf_server_drain", "mf_server_latency",
-                 "mf_server_get_stats", "mf_server_close"):
+                 "mf_server_get_stats", "mf_server_close", "mf_engine_submit_batch",
+                 "mf_server_submit_batch", "mf_server_tune"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -411,3 +421,31 @@ def mf_server_get_stats(s):
 
 def mf_server_close(s):
     _check(lib.mf_server_close(s), "mf_server_close")
+
+
+def mf_clock_ns():
+    return lib.mf_clock_ns()
+
+
+def mf_engine_submit_batch(e, pushes):
+    """pushes: numpy array of PUSH_DTYPE records (addresses as integers)."""
+    pushes = np.ascontiguousarray(pushes, dtype=PUSH_DTYPE)
+    acc = ctypes.c_int32()
+    _check(lib.mf_engine_submit_batch(e, len(pushes), pushes.ctypes.data, ctypes.byref(acc)),
+           "mf_engine_submit_batch")
+    return acc.value
+
+
+def mf_server_submit_batch(s, pushes):
+    pushes = np.ascontiguousarray(pushes, dtype=PUSH_DTYPE)
+    acc = ctypes.c_int32()
+    _check(lib.mf_server_submit_batch(s, len(pushes), pushes.ctypes.data, ctypes.byref(acc)),
+           "mf_server_submit_batch")
+    return acc.value
+
+
+def mf_server_tune(s, width, height, window):
+    b = ctypes.c_int32()
+    _check(lib.mf_server_tune(s, int(width), int(height), int(window), ctypes.byref(b)),
+           "mf_server_tune")
+    return b.value

@@ -120,6 +120,10 @@ struct mf_engine {
   bool own_stream = false;
   std::vector<Slot> slots;
   SlotParams* slots_dev = nullptr;  // max_streams + 1 entries (the last: tuner)
+  SlotParams* slots_pinned = nullptr;  // host staging of slot uploads (pinned)
+  double* ring_pool = nullptr;       // pose histories of all slots (allocated at open)
+  int32_t* bad_pool = nullptr;
+  int64_t ring_cap = 0;              // poses per slot history
   FrameRec* recs = nullptr;
   size_t tab_bytes = 0;
   char* host_tab[2] = {nullptr, nullptr};
@@ -136,7 +140,7 @@ struct mf_engine {
   std::vector<TickFrame> frames;
   std::vector<double> poses;
   int64_t next_tick = 0;
-  std::map<std::tuple<int, int, int>, int> tuned;  // (width, height, window) -> band_h
+  std::map<std::tuple<int, int, int>, int> tuned;  // (width, height, window bucket) -> band_h
   // statistics
   int64_t ticks = 0, frames_done = 0, units_done = 0, launches = 0, graph_launches = 0;
   int64_t device_bytes = 0;
@@ -252,11 +256,9 @@ void destroy(mf_engine* e) {
     cudaEventDestroy(t.first);
     cudaEventDestroy(t.second);
   }
-  for (Slot& s : e->slots) {
-    if (!s.used) continue;
-    e->dfree(s.ring, (size_t)s.ring_cap * 12 * sizeof(double));
-    e->dfree(s.ring_bad, (size_t)s.ring_cap * sizeof(int32_t));
-  }
+  e->dfree(e->ring_pool, (size_t)e->d.max_streams * e->ring_cap * 12 * sizeof(double));
+  e->dfree(e->bad_pool, (size_t)e->d.max_streams * e->ring_cap * sizeof(int32_t));
+  if (e->slots_pinned) cudaFreeHost(e->slots_pinned);
   for (int b = 0; b < 2; ++b) {
     if (e->exec[b]) cudaGraphExecDestroy(e->exec[b]);
     if (e->graph[b]) cudaGraphDestroy(e->graph[b]);
@@ -342,7 +344,11 @@ std::vector<int> band_candidates(int height) {
   return out;
 }
 
+// Tuning classes: resolution and the window rounded up to 8, 16 or 32 points.
+int window_bucket(int window) { return window <= 8 ? 8 : (window <= 16 ? 16 : 32); }
+
 int tune_class(mf_engine* e, int width, int height, int window, int* band_out) {
+  window = window_bucket(window);
   const auto key = std::make_tuple(width, height, window);
   auto it = e->tuned.find(key);
   if (it != e->tuned.end()) {
@@ -501,6 +507,14 @@ int mf_engine_open(const mf_engine_desc* d, mf_engine** out) {
     return fail(MF_ERR_CUDA, "capture stream creation");
   }
   e->slots_dev = (SlotParams*)e->dalloc((size_t)(d->max_streams + 1) * sizeof(SlotParams));
+  // every slot's pose history is allocated now, so admission never allocates
+  e->ring_cap = pow2_at_least(std::max<int64_t>(128, MF_MAX_HISTORY - 1 + d->max_stream_frames));
+  e->ring_pool = (double*)e->dalloc((size_t)d->max_streams * e->ring_cap * 12 * sizeof(double));
+  e->bad_pool = (int32_t*)e->dalloc((size_t)d->max_streams * e->ring_cap * sizeof(int32_t));
+  if (cudaMallocHost(&e->slots_pinned, (size_t)(d->max_streams + 1) * sizeof(SlotParams)) != cudaSuccess) {
+    cudaGetLastError();
+    e->slots_pinned = nullptr;
+  }
   e->recs = (FrameRec*)e->dalloc((size_t)d->max_tick_frames * sizeof(FrameRec));
   e->tab_bytes = table_bytes(d->max_tick_frames, d->max_streams, e->poses_cap());
   for (int b = 0; b < 2; ++b) {
@@ -511,7 +525,8 @@ int mf_engine_open(const mf_engine_desc* d, mf_engine** out) {
     }
     if (cudaEventCreateWithFlags(&e->done[b], cudaEventDisableTiming) != cudaSuccess) e->done[b] = nullptr;
   }
-  if (!e->slots_dev || !e->recs || !e->dev_tab[0] || !e->dev_tab[1] || !e->host_tab[0] ||
+  if (!e->slots_dev || !e->ring_pool || !e->bad_pool || !e->slots_pinned || !e->recs ||
+      !e->dev_tab[0] || !e->dev_tab[1] || !e->host_tab[0] ||
       !e->host_tab[1] || !e->done[0] || !e->done[1]) {
     destroy(e);
     return fail(MF_ERR_OOM, "engine allocation");
@@ -559,10 +574,9 @@ int mf_engine_add_stream(mf_engine* e, const mf_stream_desc* d, int64_t reserve_
       break;
     }
   if (free_slot < 0) return fail(MF_ERR_ADMISSION, "every stream slot is taken");
-  const int64_t cap = pow2_at_least(std::max<int64_t>(
-      128, (int64_t)d->window + d->smooth_len - 1 + e->d.max_stream_frames));
-  const int64_t need = cap * (12 * (int64_t)sizeof(double) + (int64_t)sizeof(int32_t)) + reserve_bytes;
-  if (e->d.memory_budget > 0 && e->accounted() + need > e->d.memory_budget)
+  // the slot's history is part of the engine's memory already; the budget
+  // admits the caller's reservation on top of it
+  if (e->d.memory_budget > 0 && e->accounted() + reserve_bytes > e->d.memory_budget)
     return fail(MF_ERR_ADMISSION, "device memory budget exhausted");
   double w[mf::kMaxHist] = {};
   if (!mf::host_ls_weights(d->smooth_len, d->mode, w))
@@ -576,26 +590,21 @@ int mf_engine_add_stream(mf_engine* e, const mf_stream_desc* d, int64_t reserve_
   Slot& s = e->slots[free_slot];
   s = Slot();
   s.d = *d;
-  s.ring_cap = cap;
-  s.ring = (double*)e->dalloc((size_t)cap * 12 * sizeof(double));
-  s.ring_bad = (int32_t*)e->dalloc((size_t)cap * sizeof(int32_t));
-  if (!s.ring || !s.ring_bad) {
-    e->dfree(s.ring, (size_t)cap * 12 * sizeof(double));
-    e->dfree(s.ring_bad, (size_t)cap * sizeof(int32_t));
-    s = Slot();
-    return fail(MF_ERR_OOM, "pose history allocation");
-  }
+  s.ring_cap = e->ring_cap;
+  s.ring = e->ring_pool + (size_t)free_slot * e->ring_cap * 12;
+  s.ring_bad = e->bad_pool + (size_t)free_slot * e->ring_cap;
   s.reserve = reserve_bytes;
   s.plane_in = (size_t)d->width * d->height * dtype_bytes(d->depth_dtype);
   s.plane_out = (size_t)d->width * d->height * dtype_bytes(d->map_dtype);
   s.band_h = band;
   s.bands = (d->height + band - 1) / band;
   s.groups_x = (d->width + mf::kEngineGroupW - 1) / mf::kEngineGroupW;
-  SlotParams sp;
-  fill_slot_params(s, w, &sp);
-  ENG_CUDA(cudaMemcpyAsync(e->slots_dev + free_slot, &sp, sizeof(sp), cudaMemcpyHostToDevice, e->st),
+  // stream-ordered upload from pinned staging: earlier ticks never read this
+  // slot (it was free), later ticks see it; nothing waits
+  fill_slot_params(s, w, e->slots_pinned + free_slot);
+  ENG_CUDA(cudaMemcpyAsync(e->slots_dev + free_slot, e->slots_pinned + free_slot, sizeof(SlotParams),
+                           cudaMemcpyHostToDevice, e->st),
            "slot upload");
-  ENG_CUDA(cudaStreamSynchronize(e->st), "slot upload");
   s.used = true;
   *slot = free_slot;
   return MF_OK;
@@ -607,10 +616,10 @@ int mf_engine_remove_stream(mf_engine* e, int32_t slot) {
   Slot& s = e->slots[slot];
   if (s.pending_tick == e->next_tick) return fail(MF_ERR_INVALID_ARG, "the stream has a queued push");
   DeviceGuard guard(e->device);
+  // the slot's pinned staging and history may be reused by the next
+  // admission only once the ticks that used them are done
   int rc = wait_tick(e, s.last_tick, -1);
   if (rc) return rc;
-  e->dfree(s.ring, (size_t)s.ring_cap * 12 * sizeof(double));
-  e->dfree(s.ring_bad, (size_t)s.ring_cap * sizeof(int32_t));
   s = Slot();
   return MF_OK;
 }
@@ -684,6 +693,21 @@ int mf::engine_submit_at(mf_engine* e, int32_t slot, int32_t n, const double* po
 }
 
 extern "C" {
+
+int64_t mf_clock_ns(void) { return now_ns(); }
+
+int mf_engine_submit_batch(mf_engine* e, int32_t n, const mf_push* pushes, int32_t* accepted) {
+  if (!e || (n > 0 && !pushes) || !accepted || n < 0) return fail(MF_ERR_INVALID_ARG, "bad batch");
+  *accepted = 0;
+  for (int32_t i = 0; i < n; ++i) {
+    const mf_push& p = pushes[i];
+    const int rc = mf::engine_submit_at(e, p.slot, p.n, p.poses_w2c_3x4, p.depth, p.K, p.focus_map,
+                                        p.guided_depth, p.info, p.arrival_ns ? p.arrival_ns : now_ns());
+    if (rc) return rc;
+    ++*accepted;
+  }
+  return MF_OK;
+}
 
 int mf_engine_tick(mf_engine* e, int64_t* tick) {
   if (!e || !tick) return fail(MF_ERR_INVALID_ARG, "NULL argument");
@@ -771,7 +795,7 @@ int mf_engine_tune(mf_engine* e, int32_t width, int32_t height, int32_t window, 
     return fail(MF_ERR_INVALID_ARG, "bad tuning request");
   if (!e->frames.empty()) return fail(MF_ERR_NOT_READY, "a tick is being assembled");
   DeviceGuard guard(e->device);
-  e->tuned.erase(std::make_tuple(width, height, window));
+  e->tuned.erase(std::make_tuple(width, height, window_bucket(window)));
   return tune_class(e, width, height, window, band_h);
 }
 

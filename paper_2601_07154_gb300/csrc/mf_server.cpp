@@ -182,36 +182,74 @@ int mf_server_add_stream(mf_server* s, const mf_stream_desc* d, int64_t reserve_
   return MF_OK;
 }
 
+namespace {
+
+// Queues one push; the caller holds s->mu.
+int enqueue(mf_server* s, const mf_push& p, int64_t t_now) {
+  if (p.slot < 0 || p.slot >= (int32_t)s->slots.size()) return fail(MF_ERR_INVALID_ARG, "no such stream");
+  if (p.n < 1 || !p.poses_w2c_3x4 || !p.K) return fail(MF_ERR_INVALID_ARG, "n < 1 or NULL poses/K");
+  if (s->err) return s->err;
+  ServerSlot& sl = s->slots[p.slot];
+  if (!sl.used) return fail(MF_ERR_INVALID_ARG, "no such stream");
+  if ((int32_t)sl.queue.size() >= s->d.queue_limit) return fail(MF_ERR_NOT_READY, "stream queue full");
+  const int O = (sl.local && sl.pushes > 0) ? sl.overlap : 0;
+  if (p.n <= O) return fail(MF_ERR_INVALID_ARG, "batch must hold more frames than the overlap");
+  if (p.n - O > s->d.engine.max_stream_frames)
+    return fail(MF_ERR_INVALID_ARG, "push exceeds max_stream_frames");
+  QueuedPush q;
+  q.t_submit = p.arrival_ns ? p.arrival_ns : t_now;
+  q.n = p.n;
+  q.n_emit = p.n - O;
+  q.poses.assign(p.poses_w2c_3x4, p.poses_w2c_3x4 + (size_t)p.n * 12);
+  q.depth = p.depth;
+  for (int k = 0; k < 4; ++k) q.K[k] = p.K[k];
+  q.M = p.focus_map;
+  q.G = p.guided_depth;
+  q.info = p.info;
+  ++sl.pushes;
+  sl.frames_submitted += q.n_emit;
+  sl.queue.push_back(std::move(q));
+  ++s->queued;
+  return MF_OK;
+}
+
+}  // namespace
+
 int mf_server_submit(mf_server* s, int32_t slot, int32_t n, const double* poses, const void* depth,
                      const double* K, void* focus_map, void* guided_depth, mf_frame_info* info) {
-  if (!s || slot < 0 || slot >= (int32_t)s->slots.size()) return fail(MF_ERR_INVALID_ARG, "no such stream");
-  if (n < 1 || !poses || !K) return fail(MF_ERR_INVALID_ARG, "n < 1 or NULL poses/K");
-  QueuedPush q;
-  q.t_submit = mf::engine_now_ns();
-  q.n = n;
-  q.poses.assign(poses, poses + (size_t)n * 12);
-  q.depth = depth;
-  for (int k = 0; k < 4; ++k) q.K[k] = K[k];
-  q.M = focus_map;
-  q.G = guided_depth;
-  q.info = info;
+  if (!s) return fail(MF_ERR_INVALID_ARG, "NULL server");
+  mf_push p{};
+  p.slot = slot;
+  p.n = n;
+  p.poses_w2c_3x4 = poses;
+  p.depth = depth;
+  p.K = K;
+  p.focus_map = focus_map;
+  p.guided_depth = guided_depth;
+  p.info = info;
+  int rc;
   {
     std::lock_guard<std::mutex> lk(s->mu);
-    if (s->err) return s->err;
-    ServerSlot& sl = s->slots[slot];
-    if (!sl.used) return fail(MF_ERR_INVALID_ARG, "no such stream");
-    if ((int32_t)sl.queue.size() >= s->d.queue_limit) return fail(MF_ERR_NOT_READY, "stream queue full");
-    const int O = (sl.local && sl.pushes > 0) ? sl.overlap : 0;
-    if (n <= O) return fail(MF_ERR_INVALID_ARG, "batch must hold more frames than the overlap");
-    q.n_emit = n - O;
-    if (q.n_emit > s->d.engine.max_stream_frames) return fail(MF_ERR_INVALID_ARG, "push exceeds max_stream_frames");
-    ++sl.pushes;
-    sl.frames_submitted += q.n_emit;
-    sl.queue.push_back(std::move(q));
-    ++s->queued;
+    rc = enqueue(s, p, mf::engine_now_ns());
   }
-  s->cv.notify_all();
-  return MF_OK;
+  if (rc == MF_OK) s->cv.notify_all();
+  return rc;
+}
+
+int mf_server_submit_batch(mf_server* s, int32_t n, const mf_push* pushes, int32_t* accepted) {
+  if (!s || !accepted || n < 0 || (n > 0 && !pushes)) return fail(MF_ERR_INVALID_ARG, "bad batch");
+  *accepted = 0;
+  int rc = MF_OK;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    const int64_t t = mf::engine_now_ns();
+    for (int32_t i = 0; i < n && rc == MF_OK; ++i) {
+      rc = enqueue(s, pushes[i], t);
+      if (rc == MF_OK) ++*accepted;
+    }
+  }
+  if (*accepted) s->cv.notify_all();
+  return rc;
 }
 
 int mf_server_frames_done(mf_server* s, int32_t slot, int64_t* frames) {
@@ -257,6 +295,12 @@ int mf_server_latency(mf_server* s, mf_latency_stats* out, int32_t reset) {
   if (!s) return fail(MF_ERR_INVALID_ARG, "NULL server");
   std::lock_guard<std::mutex> eg(s->emu);
   return mf_engine_latency(s->eng, out, reset);
+}
+
+int mf_server_tune(mf_server* s, int32_t width, int32_t height, int32_t window, int32_t* band_h) {
+  if (!s) return fail(MF_ERR_INVALID_ARG, "NULL server");
+  std::lock_guard<std::mutex> eg(s->emu);
+  return mf_engine_tune(s->eng, width, height, window, band_h);
 }
 
 int mf_server_get_stats(mf_server* s, mf_engine_stats* out) {

@@ -270,6 +270,10 @@ class MotionFocusServer:
     def frames_done(self, slot):
         return _mf.mf_server_frames_done(self.handle, slot)
 
+    def tune(self, width, height, window):
+        with torch.cuda.device(self.device):
+            return _mf.mf_server_tune(self.handle, width, height, window)
+
     def remove_stream(self, slot):
         _mf.mf_server_remove_stream(self.handle, slot)
 

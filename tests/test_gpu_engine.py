@@ -163,7 +163,7 @@ def test_engine_admission_by_memory_and_slots(mf):
                                  device=dev)
     base = sizer.stats().device_bytes                      # tables of this configuration
     sizer.close()
-    budget = base + 2 * (1 << 20) + 2 * 128 * 100          # two 128-pose histories + reserves
+    budget = base + 2 * (1 << 20)                          # two streams' reservations
     eng = mf.MotionFocusEngine(max_streams=8, max_tick_frames=64, max_stream_frames=8,
                                memory_budget=budget, device=dev)
     eng.add_stream(64, 48, window=8, smooth_len=5, reserve_bytes=1 << 20)
@@ -246,4 +246,34 @@ def test_engine_tune_picks_a_candidate(mf):
     eng = mf.MotionFocusEngine(max_streams=2, max_tick_frames=256, device=dev)
     band = eng.tune(1920, 1080, 16)
     assert 1 <= band <= 256 and (1080 + band - 1) // band * band >= 1080
+    eng.close()
+
+
+def test_engine_submit_batch_equals_single_submits(mf):
+    dev = torch.device("cuda", 0)
+    specs = STREAMS[:3]
+    single, _ = _run_engine(mf, specs)
+    eng = mf.MotionFocusEngine(max_streams=8, max_tick_frames=512, max_stream_frames=64, device=dev)
+    recs, keep = [], []
+    for spec in specs:
+        width, height, window, smooth_len, mode, seed, frames = spec
+        poses, depth, K = _inputs(spec)
+        slot = eng.add_stream(width, height, window=window, smooth_len=smooth_len, mode=mode)
+        n = min(frames, 40)
+        P = np.ascontiguousarray(poses[:n])
+        D = torch.from_numpy(depth[:n]).to(dev)
+        Kh = np.ascontiguousarray(K, dtype=np.float64)
+        M = torch.zeros((n, height, width), device=dev)
+        G = torch.zeros_like(M)
+        info = torch.zeros(n * 64, dtype=torch.uint8, device=dev)
+        keep.append((P, D, Kh, M, G, info))
+        recs.append((slot, n, P.ctypes.data, D.data_ptr(), Kh.ctypes.data, M.data_ptr(),
+                     G.data_ptr(), info.data_ptr(), 0))
+    assert mf.mf_engine_submit_batch(eng.handle, np.array(recs, dtype=mf.PUSH_DTYPE)) == 3
+    eng.wait(eng.tick())
+    for (P, D, Kh, M, G, info), ref in zip(keep, single):
+        n = M.shape[0]
+        assert np.array_equal(M.cpu().numpy(), ref[0][:n])
+        assert np.array_equal(G.cpu().numpy(), ref[1][:n])
+        assert np.array_equal(info.cpu().numpy().view(mf.FRAME_INFO_DTYPE), ref[2][:n])
     eng.close()
