@@ -166,6 +166,25 @@ def make_inputs(torch, dev, frames):
     return w, poses, depth
 
 
+def combine_ranks(torch, dist, ms_local, frames_local, world, dev):
+    """Whole-job timing: the slowest rank's time, every rank's frames.
+
+    Replicas process independent streams (no data exchange); the only
+    collectives are this reduction and the barriers around the timed region.
+    """
+    ms = ms_local
+    frames = frames_local
+    if world > 1:
+        t = torch.tensor([ms_local, float(frames_local)], device=dev, dtype=torch.float64)
+        mx = t.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = t.clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        ms = float(mx[0].item())
+        frames = float(sm[1].item())
+    return ms, frames / (ms / 1000.0)
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -218,11 +237,7 @@ def run_gpu(args):
     launches = mf.mf_total_kernel_launches() - l0
     s1 = s.stats()
     map_ms = (s1.map_kernel_ms - s0.map_kernel_ms) / max(1, s1.map_launches - s0.map_launches)
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = frames * args.steps * world / (ms / 1000.0)
+    ms, value = combine_ranks(torch, dist, ms, frames * args.steps, world, dev)
 
     prec = None
     if rank == 0 and not args.no_precision:
@@ -240,12 +255,14 @@ def run_gpu(args):
                    "plain_f32": run_batched(torch, mf, dev, args, pools32, torch.float32, plain=True)}
         for k in ("engine_f32", "engine_bf16"):
             batched[k]["vs_plain_f32"] = round(batched[k]["value"] / batched["plain_f32"]["value"], 3)
-        served = {"workload": "Poisson arrivals 4/s of 30 fps streams (mean 32 s), 128 live at "
-                              "start, cap 256, mixed resolutions, admission by memory budget "
-                              f"{args.serve_budget_gb} GB",
-                  "server_bf16": run_served(torch, mf, dev, args, pools16, torch.bfloat16),
-                  "server_f32": run_served(torch, mf, dev, args, pools32, torch.float32),
-                  "plain_f32": run_served(torch, mf, dev, args, pools32, torch.float32, plain=True)}
+        if not args.no_served:
+            served = {"workload": "Poisson arrivals 4/s of 30 fps streams (mean 32 s), 128 live "
+                                  "at start, cap 256, mixed resolutions, admission by memory "
+                                  f"budget {args.serve_budget_gb} GB",
+                      "server_bf16": run_served(torch, mf, dev, args, pools16, torch.bfloat16),
+                      "server_f32": run_served(torch, mf, dev, args, pools32, torch.float32),
+                      "plain_f32": run_served(torch, mf, dev, args, pools32, torch.float32,
+                                              plain=True)}
         del pools32, pools16
     e2e = None
     if rank == 0 and not args.no_e2e:
@@ -413,7 +430,7 @@ def run_batched(torch, mf, dev, args, pools, dtype, plain=False):
     else:
         eng = mf.MotionFocusEngine(max_streams=n_streams, max_tick_frames=n_streams * F,
                                    max_stream_frames=F, depth_dtype=dtype, map_dtype=dtype,
-                                   device=dev, cuda_stream=st)
+                                   device=dev, cuda_stream=st, tune=not args.no_tune)
         slots = [eng.add_stream(s["w"], s["h"], window=s["win"], smooth_len=SMOOTH) for s in streams]
         rec = np.zeros(n_streams, dtype=mf.PUSH_DTYPE)
         rec["slot"] = slots
@@ -693,7 +710,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
-    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-serving", action="store_true", help="skip the batched and served legs")
+    ap.add_argument("--no-served", action="store_true", help="skip the served leg")
+    ap.add_argument("--no-tune", action="store_true", help="engine legs use the plain tile height")
     ap.add_argument("--batch-frames", type=int, default=8)
     ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--serve-seconds", type=float, default=12.0)

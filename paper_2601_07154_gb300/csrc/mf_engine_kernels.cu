@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(kMapThreads, 2) engine_map_kernel(EngineKernel
   const TickPush* pushes = tick_pushes(tab);
   float* Ey = reinterpret_cast<float*>(smem4);
   uint4* ring = reinterpret_cast<uint4*>(Ey + (size_t)kBandMax * kMaxPts);
-  uint4* my_ring = ring + (size_t)(threadIdx.x >> 5) * kStages * 32;
+  uint4* my_ring = ring + (size_t)(threadIdx.x >> 5) * ring_stages(kEngineCPT) * 32;
   for (long long u = blockIdx.x; u < units; u += gridDim.x) {
     // frame owning unit u: the last frame whose unit_begin <= u
     int lo = 0, hi = nf - 1;
@@ -102,7 +102,7 @@ __global__ void engine_finalize_kernel(EngineKernelArgs a) {
   finalize_frame(a.recs + t, sp.fp.width, fr.info);
 }
 
-size_t engine_map_smem() { return unit_smem_bytes(kMaxPts, kBandMax); }
+size_t engine_map_smem() { return unit_smem_bytes(kMaxPts, kBandMax, kEngineCPT); }
 
 namespace {
 

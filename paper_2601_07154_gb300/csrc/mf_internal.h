@@ -14,7 +14,7 @@ constexpr int kMaxPts = MF_MAX_WINDOW;   // N motion points per frame
 constexpr int kMaxHist = MF_MAX_HISTORY; // W + K - 1 poses per frame
 constexpr int kTileW = 128;              // map-kernel tile width (32 lanes x 4 px)
 constexpr int kMapThreads = 256;         // 8 warps per map CTA
-constexpr int kStages = 6;               // depth rows in flight per map warp
+constexpr int kStages = 4;               // depth rows in flight per map warp (power of 2)
 constexpr int kBandMax = 256;            // rows per map unit
 constexpr int kGroupStrips = 8;          // strips (one per warp) per map unit
 

@@ -254,7 +254,7 @@ template <int NMAX, int CPT, typename TIn, typename TOut>
 __global__ void __launch_bounds__(kMapThreads, 2) map_stream_kernel(MapParams p, int band_h) {
   extern __shared__ float4 smem4[];
   float* Ey = reinterpret_cast<float*>(smem4);                          // [band_h][NMAX]
-  uint4* ring = reinterpret_cast<uint4*>(Ey + (size_t)band_h * NMAX);   // [8][kStages][32]
+  uint4* ring = reinterpret_cast<uint4*>(Ey + (size_t)band_h * NMAX);   // [8][stages][32]
   __shared__ PointsSmem<kMaxPts> P;
   __shared__ int s_kept;
   constexpr int kGroupW = kGroupStrips * 32 * CPT;
@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(kMapThreads, 2) map_stream_kernel(MapParams p,
   const int bands = (p.height + band_h - 1) / band_h;
   const long long units = (long long)p.n_frames * bands * groups_x;
   const size_t plane = (size_t)p.width * (size_t)p.height;
-  uint4* my_ring = ring + (size_t)(threadIdx.x >> 5) * kStages * 32;
+  uint4* my_ring = ring + (size_t)(threadIdx.x >> 5) * ring_stages(CPT) * 32;
   for (long long u = blockIdx.x; u < units; u += gridDim.x) {
     const int f = (int)(u / ((long long)bands * groups_x));
     const int rem = (int)(u - (long long)f * bands * groups_x);
@@ -316,12 +316,12 @@ cudaError_t launch_typed(const MapParams& p, cudaStream_t st) {
     const int band_h = (p.height + bands - 1) / bands;
     auto k = map_stream_kernel<NMAX, CPT, TIn, TOut>;
     static int per_sm = -1, sms = 0;
-    if (per_sm < 0) occupancy(k, unit_smem_bytes(NMAX, kBandMax), &per_sm, &sms);
+    if (per_sm < 0) occupancy(k, unit_smem_bytes(NMAX, kBandMax, CPT), &per_sm, &sms);
     constexpr int kGroupW = kGroupStrips * 32 * CPT;
     const long long units =
         (long long)p.n_frames * bands * ((p.width + kGroupW - 1) / kGroupW);
     const long long grid = std::min<long long>(units, (long long)sms * per_sm);
-    k<<<(unsigned)grid, kMapThreads, unit_smem_bytes(NMAX, band_h), st>>>(p, band_h);
+    k<<<(unsigned)grid, kMapThreads, unit_smem_bytes(NMAX, band_h, CPT), st>>>(p, band_h);
   } else {
     const size_t smem = (size_t)NMAX * kTileW * 4 + (size_t)p.tile_h * NMAX * 4;
     auto k = map_kernel<NMAX, TIn, TOut, false>;

@@ -15,7 +15,7 @@
 //   * each warp owns one strip: every lane holds its CPT columns' factors for
 //     the kept points in registers and streams the band's rows two at a time
 //     (CPT/2 x 2 independent FMA chains), depth arriving through the warp's
-//     ring of kStages cp.async stages, maps leaving through streaming stores.
+//     ring of cp.async stages, maps leaving through streaming stores.
 // The map is a sum of N isotropic Gaussians, so each term factors as
 //     exp(-((x-u)^2 + (y-v)^2) c) = exp(-(x-u)^2 c) * exp(-(y-v)^2 c),
 // c = 1/(2 sigma_i^2); every pixel then costs one FP32 FMA per kept point,
@@ -31,6 +31,10 @@
 namespace mf {
 
 constexpr float kCullBelow = 9.094947017729282e-13f;  // 2^-40
+
+// Depth rows in flight per warp: lanes reading 2 pixels per row need twice
+// the stages to keep the same bytes in flight.
+__host__ __device__ constexpr int ring_stages(int cpt) { return cpt >= 4 ? kStages : 2 * kStages; }
 
 template <int NMAX>
 struct PointsSmem {
@@ -65,9 +69,10 @@ __device__ __forceinline__ float2 ffma2(float2 a, float b, float2 c) {
   return d;
 }
 
-// min(1, d0 / D) for finite D > 0, else 0 (NaN fails both comparisons).
+// min(1, d0 / D) for finite D > 0, else 0: NaN and D <= 0 fail the
+// comparison, and D = +inf gives d0 * rcp(inf) = 0 by itself.
 __device__ __forceinline__ float depth_weight(float D, float d0) {
-  return (D > 0.0f && D <= 3.402823466e38f) ? fminf(1.0f, __fdividef(d0, D)) : 0.0f;
+  return D > 0.0f ? fminf(1.0f, __fdividef(d0, D)) : 0.0f;
 }
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -211,6 +216,7 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
                                          PointsSmem<kMaxPts>& P, int& s_kept) {
   constexpr int kInBytes = CPT * (int)sizeof(TIn);
   constexpr int kStrip = 32 * CPT;
+  constexpr int S = ring_stages(CPT);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int rows = ug.rows, y0 = ug.y0;
   const int x0 = ug.gx0 + warp * kStrip;
@@ -220,16 +226,17 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
   const size_t row0 = (size_t)y0 * ug.width + xc;
   const char* dsrc = ug.depth ? ug.depth + row0 * sizeof(TIn) : nullptr;
   const size_t dstride = (size_t)ug.width * sizeof(TIn);
+  static_assert((S & (S - 1)) == 0, "ring stages must be a power of two");
   auto issue = [&](int r) {
     if (r < rows && col_ok && dsrc)
-      cp_async<kInBytes>(my_ring + (r % kStages) * 32 + lane, dsrc + (size_t)r * dstride);
+      cp_async<kInBytes>(my_ring + (r & (S - 1)) * 32 + lane, dsrc + (size_t)r * dstride);
     cp_async_commit();
   };
   // The first depth rows are requested before the set-up, so the copies are
   // in flight while the factors are computed.  The ring is this warp's own
   // and the previous unit drained it.
 #pragma unroll
-  for (int s = 0; s < kStages - 2; ++s) issue(s);
+  for (int s = 0; s < S - 2; ++s) issue(s);
   __syncthreads();  // the previous unit is done with P and Ey
 
   FrameRec* rec = ug.rec;
@@ -291,20 +298,23 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
 
   float best = -1.0f;
   unsigned bidx = 0;
-  auto emit = [&](const float2 (&acc)[CPT / 2], const float (&dv)[CPT], int r) {
+  // output rows advance by a stride: no per-row 64-bit multiply
+  char* mrow = ug.M ? ug.M + row0 * sizeof(TOut) : nullptr;
+  char* grow = ug.G ? ug.G + row0 * sizeof(TOut) : nullptr;
+  const size_t ostride = (size_t)ug.width * sizeof(TOut);
+  auto emit = [&](const float2 (&acc)[CPT / 2], const float (&dv)[CPT], int r, size_t off) {
     float m[CPT];
 #pragma unroll
     for (int c = 0; c < CPT / 2; ++c) {
       m[2 * c] = acc[c].x;
       m[2 * c + 1] = acc[c].y;
     }
-    const size_t idx = row0 + (size_t)r * ug.width;
-    if (ug.M) Vec<TOut, CPT>::store(ug.M, idx, m);
-    if (ug.G) {
+    if (mrow) Vec<TOut, CPT>::store(mrow + off, 0, m);
+    if (grow) {
       float gv[CPT];
 #pragma unroll
       for (int c = 0; c < CPT; ++c) gv[c] = m[c] * depth_weight(dv[c], ug.d0);
-      Vec<TOut, CPT>::store(ug.G, idx, gv);
+      Vec<TOut, CPT>::store(grow + off, 0, gv);
     }
     float mm = m[0];
 #pragma unroll
@@ -319,19 +329,20 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
     }
   };
   // Rows r and r+1 per iteration: the ring slots of rows r-2 and r-1 were
-  // consumed by the previous iteration, so rows r+kStages-2 and r+kStages-1
+  // consumed by the previous iteration, so rows r+S-2 and r+S-1
   // can be requested before rows r, r+1 are read.
-  for (int r = 0; r < rows; r += 2) {
-    issue(r + kStages - 2);
-    issue(r + kStages - 1);
-    cp_async_wait<kStages - 2>();
+  size_t off = 0;
+  for (int r = 0; r < rows; r += 2, off += 2 * ostride) {
+    issue(r + S - 2);
+    issue(r + S - 1);
+    cp_async_wait<S - 2>();
     const bool two = r + 1 < rows;
     float d0v[CPT], d1v[CPT];
 #pragma unroll
     for (int c = 0; c < CPT; ++c) d0v[c] = d1v[c] = 0.0f;
     if (dsrc) {
-      Vec<TIn, CPT>::unpack(my_ring[(r % kStages) * 32 + lane], d0v);
-      if (two) Vec<TIn, CPT>::unpack(my_ring[((r + 1) % kStages) * 32 + lane], d1v);
+      Vec<TIn, CPT>::unpack(my_ring[(r & (S - 1)) * 32 + lane], d0v);
+      if (two) Vec<TIn, CPT>::unpack(my_ring[((r + 1) & (S - 1)) * 32 + lane], d1v);
     }
     float2 a[CPT / 2], b[CPT / 2];
 #pragma unroll
@@ -343,8 +354,8 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
     else
       accum_two_rows<NMAX, CPT, 0>(ex, ey0, ey1, nc, a, b);
     if (!col_ok) continue;
-    emit(a, d0v, r);
-    if (two) emit(b, d1v, r + 1);
+    emit(a, d0v, r, off);
+    if (two) emit(b, d1v, r + 1, off + ostride);
   }
   cp_async_wait<0>();
   unsigned long long key =
@@ -356,9 +367,10 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
   if (lane == 0 && n > 0 && key) atomicMax(&rec->argmax_key, key);
 }
 
-// Dynamic shared memory of a CTA running units of bucket NMAX.
-__host__ __device__ constexpr size_t unit_smem_bytes(int nmax, int band_h) {
-  return (size_t)band_h * nmax * 4 + (size_t)(kMapThreads / 32) * kStages * 32 * 16;
+// Dynamic shared memory of a CTA running units of bucket NMAX with CPT
+// pixels per lane: the band's row factors, then every warp's depth ring.
+__host__ __device__ constexpr size_t unit_smem_bytes(int nmax, int band_h, int cpt) {
+  return (size_t)band_h * nmax * 4 + (size_t)(kMapThreads / 32) * ring_stages(cpt) * 32 * 16;
 }
 
 }  // namespace mf
