@@ -242,6 +242,9 @@ def run_gpu(args):
     prec = None
     if rank == 0 and not args.no_precision:
         prec = run_precision(torch, mf, w, poses, depth, dev, args, value / world)
+    variants = None
+    if rank == 0 and not args.no_variants:
+        variants = run_variants(torch, mf, w, poses, depth, dev, args, value / world)
     batched = served = None
     if rank == 0 and not args.no_serving:
         del M, G
@@ -289,7 +292,7 @@ def run_gpu(args):
                          "algorithmic_bytes_per_launch": frames * FRAME_BYTES,
                          "launch_ms": round(map_ms, 4)},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
-            "precision": prec, "batched": batched, "served": served,
+            "precision": prec, "variants": variants, "batched": batched, "served": served,
         }
         print(json.dumps(rec), flush=True)
     if world > 1:
@@ -297,47 +300,64 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-def run_precision(torch, mf, w, poses, depth, dev, args, f32_value):
-    """The same workload with 16-bit depth and map storage (FP32 arithmetic)."""
-    out = {}
+def run_leg(torch, mf, w, poses, depth, dev, args, dt, mode="accel", normalize="count"):
+    """The default workload with another storage type, mode or normalisation."""
     frames = int(depth.shape[0])
     steps = max(10, min(args.steps, 100))
     Kh = np.ascontiguousarray(w.K())
+    din = depth if dt == torch.float32 else depth.to(dt)
+    M = torch.empty((frames, HEIGHT, WIDTH), dtype=dt, device=dev)
+    G = torch.empty_like(M)
+    info = torch.empty(frames * 64, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(dev)
+    s = mf.MotionFocusStream(WIDTH, HEIGHT, window=WINDOW, smooth_len=SMOOTH, device=dev,
+                             cuda_stream=stream, time_kernels=True, depth_dtype=dt,
+                             map_dtype=dt, mode=mode, normalize=normalize)
+    h = s.handle
+
+    def step():
+        mf.mf_reset_stream(h)
+        mf.mf_push_frames(h, frames, poses, din, Kh)
+        assert mf.mf_get_maps(h, frames, M, G, info, None) == frames
+
+    for _ in range(args.warmup):
+        step()
+    stream.synchronize()
+    s0 = s.stats()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        step()
+    ev1.record(stream)
+    ev1.synchronize()
+    s1 = s.stats()
+    ms = ev0.elapsed_time(ev1) / steps
+    map_ms = (s1.map_kernel_ms - s0.map_kernel_ms) / max(1, s1.map_launches - s0.map_launches)
+    bpp = 3 * din.element_size()
+    s.close()
+    return {"value": round(frames / (ms / 1000.0), 2), "unit": "frames/s", "steps": steps,
+            "map_gbs": round(frames * WIDTH * HEIGHT * bpp / (map_ms / 1000.0) / 1e9, 1),
+            "bytes_per_px": bpp}
+
+
+def run_precision(torch, mf, w, poses, depth, dev, args, f32_value):
+    """The same workload with 16-bit depth and map storage (FP32 arithmetic)."""
+    out = {}
     for name, dt in (("bf16", torch.bfloat16), ("f16", torch.float16)):
-        d16 = depth.to(dt)
-        M = torch.empty((frames, HEIGHT, WIDTH), dtype=dt, device=dev)
-        G = torch.empty_like(M)
-        info = torch.empty(frames * 64, dtype=torch.uint8, device=dev)
-        stream = torch.cuda.Stream(dev)
-        s = mf.MotionFocusStream(WIDTH, HEIGHT, window=WINDOW, smooth_len=SMOOTH, device=dev,
-                                 cuda_stream=stream, time_kernels=True, depth_dtype=dt,
-                                 map_dtype=dt)
-        h = s.handle
+        out[name] = run_leg(torch, mf, w, poses, depth, dev, args, dt)
+        out[name]["gain_vs_f32"] = round(out[name]["value"] / f32_value, 3)
+    return out
 
-        def step():
-            mf.mf_reset_stream(h)
-            mf.mf_push_frames(h, frames, poses, d16, Kh)
-            mf.mf_get_maps(h, frames, M, G, info, None)
 
-        for _ in range(args.warmup):
-            step()
-        stream.synchronize()
-        s0 = s.stats()
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ev0.record(stream)
-        for _ in range(steps):
-            step()
-        ev1.record(stream)
-        ev1.synchronize()
-        s1 = s.stats()
-        ms = ev0.elapsed_time(ev1) / steps
-        map_ms = (s1.map_kernel_ms - s0.map_kernel_ms) / max(1, s1.map_launches - s0.map_launches)
-        fps = frames / (ms / 1000.0)
-        out[name] = {"value": round(fps, 2), "unit": "frames/s", "steps": steps,
-                     "map_gbs": round(frames * WIDTH * HEIGHT * 6 / (map_ms / 1000.0) / 1e9, 1),
-                     "bytes_per_px": 6, "gain_vs_f32": round(fps / f32_value, 3)}
-        s.close()
-        del d16, M, G
+def run_variants(torch, mf, w, poses, depth, dev, args, f32_value):
+    """HEADING mode, and ACCEL with Z = the map maximum (an extra in-place pass
+    over both maps), on the default workload in FP32."""
+    out = {"heading_f32": run_leg(torch, mf, w, poses, depth, dev, args, torch.float32,
+                                  mode="heading"),
+           "norm_max_f32": run_leg(torch, mf, w, poses, depth, dev, args, torch.float32,
+                                   normalize="max")}
+    for v in out.values():
+        v["vs_default"] = round(v["value"] / f32_value, 3)
     return out
 
 
@@ -710,6 +730,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--no-variants", action="store_true", help="skip the HEADING / Z=max legs")
     ap.add_argument("--no-serving", action="store_true", help="skip the batched and served legs")
     ap.add_argument("--no-served", action="store_true", help="skip the served leg")
     ap.add_argument("--no-tune", action="store_true", help="engine legs use the plain tile height")

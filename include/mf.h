@@ -45,8 +45,8 @@ typedef enum { MF_F32 = 0, MF_BF16 = 1, MF_F16 = 2 } mf_dtype;
 
 /* Direction that is projected (Section 2.3):
  *   ACCEL   -- acceleration (Eqs. 2-3), the paper's motion focus;
- *   HEADING -- velocity, the "velocity-based projection" the paper contrasts
- *              with after Eq. 6. */
+ *   HEADING -- velocity: the projection of velocity that the paper compares
+ *              its method against after Eq. 6. */
 typedef enum { MF_MODE_ACCEL = 0, MF_MODE_HEADING = 1 } mf_mode;
 
 /* Coordinate frame of pushed poses (Section 2.2):
@@ -75,6 +75,14 @@ typedef enum {
   MF_FRAME_BAD_POSE = 2   /* the frame's own pose is not a rigid transform */
 } mf_frame_status;
 
+/* The normaliser Z of Eq. 7, which the paper leaves open:
+ *   COUNT -- Z = number of valid points: M in [0, 1], 1 only where every
+ *            point's Gaussian peaks (default);
+ *   MAX   -- Z = the frame's largest point sum: every non-empty map is
+ *            exactly 1 at its argmax (one extra in-place pass over M and G;
+ *            mf_frame_info.map_max is then 1). */
+typedef enum { MF_NORM_COUNT = 0, MF_NORM_MAX = 1 } mf_norm;
+
 /* mf_stream_desc.flags */
 #define MF_FLAG_TIME_KERNELS 1u /* time each map-kernel launch with CUDA events */
 
@@ -83,8 +91,7 @@ typedef enum {
  *   width, height        map resolution == depth resolution (1..MF_MAX_DIM)
  *   calib_width/height   resolution the intrinsics K refer to; 0 = same as
  *                        the map.  K is rescaled to the map resolution
- *                        ("real camera intrinsics as physical constraints",
- *                        Section 1; K of Eq. 5).
+ *                        (the intrinsics K of Eq. 5, Section 1).
  *   window               W = N motion points per frame (Eq. 7), 1..32
  *   smooth_len           K samples of the causal least-squares fit that
  *                        generalises Eqs. 2-3 (3 reproduces Eq. 3 exactly);
@@ -96,6 +103,8 @@ typedef enum {
  *   depth_dtype          storage type of pushed depth (mf_dtype)
  *   map_dtype            storage type of both output maps (mf_dtype)
  *   max_pending          frames that may wait between push and get_maps
+ *   normalize            mf_norm (MF_NORM_MAX is not available to engine
+ *                        streams)
  *   sigma_rel            sigma of Eq. 7 as a fraction of fx (default 0.1)
  *   s_lo, s_hi           clamp of the motion magnitude s_i (0.25, 4)
  *   depth_ref_m          d0 of the guided depth G = M min(1, d0/D) (1.0 m)
@@ -118,7 +127,7 @@ typedef struct {
   int32_t map_dtype;
   int32_t max_pending;
   uint32_t flags;
-  int32_t reserved0;
+  int32_t normalize;
   double sigma_rel, s_lo, s_hi, depth_ref_m;
   void* cuda_stream;
   void* (*dev_alloc)(size_t bytes, void* ctx);
@@ -136,7 +145,8 @@ typedef struct {
   double focus_u, focus_v;     /* Eq. 6 of the newest point, pixels; 0 if invalid */
   int32_t focus_px_x, focus_px_y; /* rint(focus) if inside the frame, else -1 */
   int32_t argmax_x, argmax_y;  /* largest M (ties: lowest y*width+x); -1 if empty */
-  float map_max;               /* M at the argmax (FP32 arithmetic value) */
+  float map_max;               /* M at the argmax (FP32 arithmetic value, after
+                                  the MF_NORM_MAX scaling when selected) */
   int32_t reserved;
 } mf_frame_info;
 

@@ -37,7 +37,8 @@ path's specification):
   valid iff rho > 1e-12 * max_j |p_j|, |d_i| > 1e-9 rho and |d_iz| > 1e-3 |d_i|;
   Eq. 6 is applied literally (the sign of d_z is not used);
 * s_i = clamp(|d_i| / mean_valid |d|, s_lo, s_hi), spread sigma_i =
-  sigma_rel * fx' * s_i, Z = number of valid points;
+  sigma_rel * fx' * s_i, Z = number of valid points (or, optionally, the map's
+  largest value, so that the map peaks at 1);
 * intrinsics compensation (Section 1, "real camera intrinsics as physical
   constraints"): K given at a calibration resolution is rescaled to the map
   resolution with pixel centres at integer coordinates;
@@ -82,6 +83,7 @@ class Params:
     s_lo: float = 0.25
     s_hi: float = 4.0
     depth_ref_m: float = 1.0
+    normalize: str = "count"    # Z of Eq. 7: "count" (valid points) or "max" (map maximum)
 
 
 # ---------------------------------------------------------------- Eqs. 2-3 --
@@ -389,6 +391,9 @@ class OracleStream:
         M = G = None
         if full_maps:
             M = focus_map(pts, p.width, p.height)
+            if p.normalize == "max" and M.max() > 0.0:
+                # Z = the map's largest point sum: the map peaks at exactly 1
+                M = M / M.max()
             if self.depth[n] is not None:
                 G = guided_depth(M, self.depth[n], p.depth_ref_m)
             ax, ay, mx = map_argmax(M, pts.n_valid)

@@ -19,6 +19,7 @@ MF_MODE_ACCEL, MF_MODE_HEADING = 0, 1
 MF_POSES_WORLD, MF_POSES_BATCH_LOCAL = 0, 1
 MF_FRAME_OK, MF_FRAME_EMPTY, MF_FRAME_BAD_POSE = 0, 1, 2
 MF_FLAG_TIME_KERNELS = 1
+MF_NORM_COUNT, MF_NORM_MAX = 0, 1
 (MF_OK, MF_ERR_INVALID_ARG, MF_ERR_INVALID_POSE, MF_ERR_OOM, MF_ERR_NOT_READY,
  MF_ERR_TIMEOUT, MF_ERR_CUDA, MF_ERR_ADMISSION, MF_ERR_NO_DEVICE) = range(9)
 
@@ -50,7 +51,7 @@ class MFStreamDesc(ctypes.Structure):
         ("mode", ctypes.c_int32), ("pose_frame", ctypes.c_int32),
         ("overlap", ctypes.c_int32), ("depth_dtype", ctypes.c_int32),
         ("map_dtype", ctypes.c_int32), ("max_pending", ctypes.c_int32),
-        ("flags", ctypes.c_uint32), ("reserved0", ctypes.c_int32),
+        ("flags", ctypes.c_uint32), ("normalize", ctypes.c_int32),
         ("sigma_rel", ctypes.c_double), ("s_lo", ctypes.c_double),
         ("s_hi", ctypes.c_double), ("depth_ref_m", ctypes.c_double),
         ("cuda_stream", ctypes.c_void_p),

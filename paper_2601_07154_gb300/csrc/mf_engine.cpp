@@ -567,6 +567,8 @@ int mf_engine_add_stream(mf_engine* e, const mf_stream_desc* d, int64_t reserve_
     return fail(MF_ERR_INVALID_ARG, "stream dtypes differ from the engine's");
   if (reserve_bytes < 0) return fail(MF_ERR_INVALID_ARG, "negative reservation");
   if (d->width % mf::kEngineCPT) return fail(MF_ERR_INVALID_ARG, "engine streams need an even width");
+  if (d->normalize != MF_NORM_COUNT)
+    return fail(MF_ERR_INVALID_ARG, "engine streams use Z = number of valid points");
   int free_slot = -1;
   for (int i = 0; i < e->d.max_streams; ++i)
     if (!e->slots[i].used) {

@@ -92,8 +92,20 @@ struct FinalizeParams {
   int64_t f0;
   int n_frames;
   int width, window;
+  int normalize;           // mf_norm: report the map maximum after scaling
   mf_frame_info* info;     // may be NULL
   mf_motion_point* points; // may be NULL
+};
+
+// In-place MF_NORM_MAX scaling of M and G by 1 / (the frame's map maximum).
+struct NormalizeParams {
+  const FrameRec* recs;
+  int64_t rec_mask;
+  int64_t f0;
+  int n_frames;
+  int64_t plane;           // pixels per frame
+  void* M;                 // plane of frame f0 (may be NULL)
+  void* G;                 // (may be NULL)
 };
 
 // Launchers (return the CUDA launch status).  `launches` is incremented by
@@ -103,6 +115,8 @@ cudaError_t launch_points(const PointsParams& p, cudaStream_t st, int64_t* launc
 cudaError_t launch_map(const MapParams& p, int window, int in_dtype, int out_dtype,
                        cudaStream_t st, int64_t* launches);
 cudaError_t launch_finalize(const FinalizeParams& p, cudaStream_t st, int64_t* launches);
+cudaError_t launch_normalize(const NormalizeParams& p, int map_dtype, cudaStream_t st,
+                             int64_t* launches);
 cudaError_t launch_ring_copy(const double* src, const int32_t* src_bad, int64_t src_mask,
                              double* dst, int32_t* dst_bad, int64_t dst_mask, int64_t first,
                              int count, cudaStream_t st, int64_t* launches);

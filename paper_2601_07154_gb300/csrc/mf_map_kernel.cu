@@ -21,6 +21,7 @@
 #include <algorithm>
 
 #include "mf_map_unit.cuh"
+#include "mf_pose_device.cuh"
 
 namespace mf {
 
@@ -280,6 +281,71 @@ __global__ void __launch_bounds__(kMapThreads, 2) map_stream_kernel(MapParams p,
     ug.d0 = p.d0;
     map_unit<NMAX, CPT, TIn, TOut>(ug, Ey, my_ring, P, s_kept);
   }
+}
+
+// ---------------------------------------------------------------------------
+// MF_NORM_MAX (Eq. 7 with Z = the frame's largest point sum): divides a
+// frame's M and G in place by its map maximum (from the fused argmax).
+// blockIdx.y is the frame; the CTAs of a frame stride over its pixels, four
+// at a time when the planes allow vector access.
+template <typename TOut, bool VEC>
+__global__ void __launch_bounds__(256) normalize_kernel(NormalizeParams p) {
+  const int f = blockIdx.y;
+  const float z = norm_divisor(p.recs + ((p.f0 + f) & p.rec_mask));
+  const size_t base = (size_t)f * p.plane;
+  const size_t step = (size_t)gridDim.x * blockDim.x;
+  if (VEC) {
+    const size_t quads = p.plane / 4;
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < quads; q += step) {
+      const size_t i = base + 4 * q;
+      float v[4];
+      for (int c = 0; c < 2; ++c) {
+        void* plane = c == 0 ? p.M : p.G;
+        if (!plane) continue;
+        const float4 x = Px<TOut>::load4(plane, i);
+        v[0] = x.x / z;
+        v[1] = x.y / z;
+        v[2] = x.z / z;
+        v[3] = x.w / z;
+        Px<TOut>::store4(plane, i, make_float4(v[0], v[1], v[2], v[3]));
+      }
+    }
+  } else {
+    for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < (size_t)p.plane; j += step) {
+      if (p.M) Px<TOut>::store1(p.M, base + j, Px<TOut>::load1(p.M, base + j) / z);
+      if (p.G) Px<TOut>::store1(p.G, base + j, Px<TOut>::load1(p.G, base + j) / z);
+    }
+  }
+}
+
+namespace {
+template <typename TOut>
+cudaError_t launch_normalize_typed(const NormalizeParams& p, cudaStream_t st) {
+  auto aligned = [](const void* q) { return q == nullptr || ((uintptr_t)q % (4 * sizeof(TOut))) == 0; };
+  const bool vec = (p.plane % 4) == 0 && aligned(p.M) && aligned(p.G);
+  const long long per = std::max<long long>(1, std::min<long long>(64, (p.plane / 4 + 255) / 256));
+  const dim3 grid((unsigned)per, (unsigned)p.n_frames);
+  if (vec)
+    normalize_kernel<TOut, true><<<grid, 256, 0, st>>>(p);
+  else
+    normalize_kernel<TOut, false><<<grid, 256, 0, st>>>(p);
+  return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_normalize(const NormalizeParams& p, int map_dtype, cudaStream_t st,
+                             int64_t* launches) {
+  if (p.n_frames <= 0 || (!p.M && !p.G)) return cudaSuccess;
+  if (p.n_frames > 65535) return cudaErrorInvalidConfiguration;
+  cudaError_t e;
+  switch (map_dtype) {
+    case MF_F32: e = launch_normalize_typed<float>(p, st); break;
+    case MF_BF16: e = launch_normalize_typed<__nv_bfloat16>(p, st); break;
+    case MF_F16: e = launch_normalize_typed<__half>(p, st); break;
+    default: return cudaErrorInvalidValue;
+  }
+  if (e == cudaSuccess) ++*launches;
+  return e;
 }
 
 int map_tile_h(int width, int height, int window) {

@@ -268,7 +268,18 @@ __device__ __forceinline__ void frame_points(const double* ring, const int32_t* 
   }
 }
 
-__device__ __forceinline__ void finalize_frame(const FrameRec* rec, int width, mf_frame_info* out) {
+// Divisor of a frame's maps under MF_NORM_MAX: the map maximum found by the
+// fused argmax, or 1 for an empty map (left as it is, all zeros).  Dividing
+// (rather than multiplying by a reciprocal) maps the maximum to exactly 1.
+__device__ __forceinline__ float norm_divisor(const FrameRec* rec) {
+  const unsigned long long key = rec->argmax_key;
+  if (rec->n_valid <= 0 || key == 0ull) return 1.0f;
+  const float mx = __uint_as_float((unsigned)(key >> 32));
+  return mx > 0.0f ? mx : 1.0f;
+}
+
+__device__ __forceinline__ void finalize_frame(const FrameRec* rec, int width, mf_frame_info* out,
+                                               int normalize = MF_NORM_COUNT) {
   mf_frame_info o;
   o.frame_index = rec->frame_index;
   o.status = rec->status;
@@ -285,6 +296,7 @@ __device__ __forceinline__ void finalize_frame(const FrameRec* rec, int width, m
     o.argmax_x = (int)(idx % (unsigned)width);
     o.argmax_y = (int)(idx / (unsigned)width);
     o.map_max = __uint_as_float((unsigned)(key >> 32));
+    if (normalize == MF_NORM_MAX && o.map_max > 0.0f) o.map_max = 1.0f;
   } else {
     o.argmax_x = -1;
     o.argmax_y = -1;

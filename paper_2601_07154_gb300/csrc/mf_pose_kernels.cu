@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(kPtsWarps * 32) points_kernel(PointsParams p) 
 __global__ void finalize_kernel(FinalizeParams p) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (p.info && t < p.n_frames)
-    finalize_frame(p.recs + ((p.f0 + t) & p.rec_mask), p.width, p.info + t);
+    finalize_frame(p.recs + ((p.f0 + t) & p.rec_mask), p.width, p.info + t, p.normalize);
   if (p.points) {
     const int total = p.n_frames * p.window;
     for (int e = t; e < total; e += gridDim.x * blockDim.x) {

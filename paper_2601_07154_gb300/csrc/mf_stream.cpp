@@ -386,6 +386,8 @@ int validate_desc(const mf_stream_desc* d) {
       return fail(MF_ERR_INVALID_ARG, "unknown dtype");
   if (d->max_pending < 1 || d->max_pending > (1 << 24))
     return fail(MF_ERR_INVALID_ARG, "max_pending out of range");
+  if (d->normalize != MF_NORM_COUNT && d->normalize != MF_NORM_MAX)
+    return fail(MF_ERR_INVALID_ARG, "unknown normalisation");
   if (!(d->sigma_rel > 0.0) || !(d->s_lo > 0.0) || !(d->s_hi >= d->s_lo) ||
       !(d->depth_ref_m > 0.0) || !std::isfinite(d->sigma_rel) || !std::isfinite(d->s_hi) ||
       !std::isfinite(d->depth_ref_m))
@@ -674,6 +676,17 @@ int mf_get_maps(mf_stream* s, int32_t max_frames, void* focus_map, void* guided_
       s->runs.pop_front();
     }
   }
+  if (s->d.normalize == MF_NORM_MAX) {
+    mf::NormalizeParams np{};
+    np.recs = s->recs;
+    np.rec_mask = s->rec_cap - 1;
+    np.f0 = s->rendered;
+    np.n_frames = (int)take;
+    np.plane = (int64_t)s->d.width * s->d.height;
+    np.M = Md;
+    np.G = Gd;
+    MF_CUDA(mf::launch_normalize(np, s->d.map_dtype, s->st, &s->launches), "normalize launch");
+  }
   mf::FinalizeParams fp{};
   fp.recs = s->recs;
   fp.rec_mask = s->rec_cap - 1;
@@ -681,6 +694,7 @@ int mf_get_maps(mf_stream* s, int32_t max_frames, void* focus_map, void* guided_
   fp.n_frames = (int)take;
   fp.width = s->d.width;
   fp.window = s->d.window;
+  fp.normalize = s->d.normalize;
   fp.info = reinterpret_cast<mf_frame_info*>(Id);
   fp.points = reinterpret_cast<mf_motion_point*>(Pd);
   MF_CUDA(mf::launch_finalize(fp, s->st, &s->launches), "finalize launch");

@@ -25,8 +25,16 @@ def coord_tol(u, v, intr):
     return 1e-3 * (1.0 + r2)
 
 
-def map_tol(ref, storage="f32"):
-    return (MAP_RTOL + STORAGE_RTOL[storage]) * np.abs(ref) + MAP_ATOL + STORAGE_ATOL[storage]
+def map_tol(ref, storage="f32", divisor=None):
+    """Per-pixel bound.  ``divisor`` (the FP64 map maximum) marks a map divided
+    by its own maximum: the quotient carries the bound of the numerator and of
+    the divisor, one FP32 division rounding, and for 16-bit storage a second
+    rounding; absolute terms scale by 1 / divisor."""
+    if divisor is None:
+        return (MAP_RTOL + STORAGE_RTOL[storage]) * np.abs(ref) + MAP_ATOL + STORAGE_ATOL[storage]
+    rtol = 2 * MAP_RTOL + 2.0 ** -24 + 2 * STORAGE_RTOL[storage]
+    atol = (MAP_ATOL + STORAGE_ATOL[storage]) / divisor + STORAGE_ATOL[storage]
+    return rtol * np.abs(ref) + atol
 
 
 def check_frame(info, pts, ref_info, ref_pts, intr, where=""):
@@ -59,10 +67,10 @@ def check_argmax(info, M_ref, n_valid, storage="f32", where=""):
     assert abs(float(info["map_max"]) - mx) <= MAP_RTOL * mx + MAP_ATOL, where
 
 
-def check_map(got, ref, storage="f32", where=""):
+def check_map(got, ref, storage="f32", where="", divisor=None):
     got = np.asarray(got, dtype=np.float64)
     err = np.abs(got - ref)
-    tol = map_tol(ref, storage)
+    tol = map_tol(ref, storage, divisor)
     bad = err > tol
     if bad.any():
         i = np.unravel_index(np.argmax(err - tol), err.shape)

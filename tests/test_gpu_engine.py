@@ -277,3 +277,54 @@ def test_engine_submit_batch_equals_single_submits(mf):
         assert np.array_equal(G.cpu().numpy(), ref[1][:n])
         assert np.array_equal(info.cpu().numpy().view(mf.FRAME_INFO_DTYPE), ref[2][:n])
     eng.close()
+
+
+def test_engine_mixed_workload_full_size_sampled(mf):
+    """Streams of the mixed workload (640x480 .. 3840x2160, windows 8..32) through
+    engine ticks of 8 frames per stream, as the benchmark runs them: every
+    frame's records exactly, 256 sampled pixels per frame and the argmax value
+    against the oracle."""
+    from synth import mixed_streams
+    dev = torch.device("cuda", 0)
+    specs = [sp for sp in mixed_streams(16, cfg=4, ring=2)][:8]
+    assert {(s.width, s.height) for s in specs} >= {(3840, 2160)}
+    frames, F = 24, 8
+    eng = mf.MotionFocusEngine(max_streams=8, max_tick_frames=8 * F, max_stream_frames=F, device=dev)
+    state = []
+    for sp in specs:
+        slot = eng.add_stream(sp.width, sp.height, window=sp.window, smooth_len=sp.smooth_len)
+        ring = torch.from_numpy(np.stack([sp.depth(k) for k in range(2)])).to(dev)
+        depth = ring[torch.arange(frames, device=dev) % 2].contiguous()
+        M = torch.zeros((frames, sp.height, sp.width), device=dev)
+        G = torch.zeros_like(M)
+        info = torch.zeros(frames * 64, dtype=torch.uint8, device=dev)
+        state.append((sp, slot, depth, M, G, info))
+    for lo in range(0, frames, F):
+        for sp, slot, depth, M, G, info in state:
+            eng.submit(slot, sp.poses[lo:lo + F], depth[lo:lo + F], sp.K(), M[lo:lo + F],
+                       G[lo:lo + F], info[lo * 64:(lo + F) * 64])
+        t = eng.tick()
+    eng.wait(t)
+    rng = np.random.default_rng(8)
+    for sp, slot, depth, M, G, info in state:
+        ref = O.OracleStream(O.Params(sp.width, sp.height, window=sp.window, smooth_len=sp.smooth_len))
+        ref.push(sp.poses[:frames], None, sp.K())
+        intr = O.compensated_intrinsics(sp.K(), ref.p)
+        infos = info.cpu().numpy().view(mf.FRAME_INFO_DTYPE)
+        ys = rng.integers(0, sp.height, 256)
+        xs = rng.integers(0, sp.width, 256)
+        yt, xt = torch.from_numpy(ys).to(dev), torch.from_numpy(xs).to(dev)
+        Ms = M[:, yt, xt].double().cpu().numpy()
+        Gs = G[:, yt, xt].double().cpu().numpy()
+        dh = depth[:, yt, xt].double().cpu().numpy()
+        for n in range(frames):
+            rinfo, rp, _, _ = ref.frame(n, full_maps=False)
+            parity.check_frame(infos[n], None, rinfo, rp, intr, where=f"{sp.name} frame {n}")
+            Mr = O.focus_map(rp, sp.width, sp.height, xs, ys)
+            parity.check_map(Ms[n], Mr, where=f"{sp.name} M {n}")
+            parity.check_map(Gs[n], O.guided_depth(Mr, dh[n], 1.0), where=f"{sp.name} G {n}")
+            if rinfo["n_valid"]:
+                ax, ay = int(infos[n]["argmax_x"]), int(infos[n]["argmax_y"])
+                m_at = O.focus_map(rp, sp.width, sp.height, np.array([ax]), np.array([ay]))[0]
+                assert abs(float(infos[n]["map_max"]) - m_at) <= 1e-5 * m_at + 1e-10
+    eng.close()

@@ -32,17 +32,17 @@ def _mode(name):
 
 def run_both(mf, poses, depth, K, width, height, window=8, smooth_len=15, mode="accel",
              storage="f32", pushes=None, pose_frame="world", overlap=0, calib=None,
-             on_host=False, get_chunks=None):
+             on_host=False, get_chunks=None, normalize="count"):
     """Run the same pushes through the GPU stream and the oracle."""
     dev = torch.device("cuda", 0)
     dt = TDT[storage]
     s = mf.MotionFocusStream(width, height, window=window, smooth_len=smooth_len, mode=mode,
                              pose_frame=pose_frame, overlap=overlap, depth_dtype=dt, map_dtype=dt,
-                             calib=calib, device=dev)
+                             calib=calib, device=dev, normalize=normalize)
     p = O.Params(width, height, window=window, smooth_len=smooth_len, mode=_mode(mode),
                  pose_frame=O.POSES_BATCH_LOCAL if pose_frame == "batch_local" else O.POSES_WORLD,
                  overlap=overlap, calib_width=calib[0] if calib else 0,
-                 calib_height=calib[1] if calib else 0)
+                 calib_height=calib[1] if calib else 0, normalize=normalize)
     ref = O.OracleStream(p)
     pushes = pushes or [(0, len(poses))]
     keep = []
@@ -179,6 +179,38 @@ def test_calibration_rescale(mf):
     M, G, info, pts, ref = run_both(mf, poses, None, K, 320, 240, window=8, smooth_len=5,
                                     mode="heading", calib=(640, 480))
     compare_all(M, G, info, pts, ref, K)
+
+
+@pytest.mark.parametrize("mode,storage", [("accel", "f32"), ("heading", "f32"),
+                                          ("heading", "bf16"), ("accel", "f16")])
+def test_max_normalised_maps(mf, mode, storage):
+    """Z = the map maximum: each frame's maps divided by its FP32 maximum."""
+    w = small_stream()
+    M, G, info, pts, ref = run_both(mf, w.poses, w.depth_stack(0, 64), w.K(), 320, 240,
+                                    window=8, smooth_len=15, mode=mode, storage=storage,
+                                    normalize="max")
+    assert len(info) == ref.n_emitted
+    cref = O.Params(320, 240, window=8, smooth_len=15, mode=_mode(mode))
+    cst = O.OracleStream(cref)
+    cst.push(w.poses, w.depth_stack(0, 64), w.K())
+    intr = O.compensated_intrinsics(w.K(), ref.p)
+    nonempty = 0
+    for n in range(ref.n_emitted):
+        rinfo, rp, Mr, Gr = ref.frame(n)
+        parity.check_frame(info[n], pts[n], rinfo, rp, intr, where=f"frame {n}")
+        if rinfo["n_valid"] == 0:
+            assert not M[n].any() and not G[n].any() and info[n]["map_max"] == 0.0
+            continue
+        nonempty += 1
+        mx = cst.frame(n)[2].max()            # the divisor, from the count map
+        parity.check_map(M[n], Mr, storage, f"M frame {n}", divisor=mx)
+        parity.check_map(G[n], Gr, storage, f"G frame {n}", divisor=mx)
+        assert info[n]["map_max"] == 1.0
+        x, y = int(info[n]["argmax_x"]), int(info[n]["argmax_y"])
+        assert Mr[y, x] >= 1.0 - 4 * parity.MAP_RTOL
+        if storage == "f32":
+            assert M[n][y, x] == 1.0 and M[n].max() == 1.0
+    assert nonempty > 40
 
 
 # ------------------------------------------------------------ edge cases --

@@ -224,6 +224,53 @@ def test_single_point_map_closed_form_and_argmax():
     assert info["map_max"] == M.max() <= 1.0
 
 
+def test_max_normalised_single_point_closed_form():
+    """Z = the map maximum: one point's map is exp(-(r^2 - r_min^2) / (2 sigma^2)),
+    r_min the distance from the point to its nearest pixel, so it peaks at 1."""
+    th, ph = 0.07, -0.04
+    p = O.Params(48, 36, window=4, smooth_len=2, mode=O.MODE_HEADING, normalize="max")
+    st = run(_const_velocity(2, (0, 0, 0.05), rot=rot_y(th) @ rot_x(ph)), p,
+             K=(40.0, 40.0, 23.5, 17.5), depth=np.full((2, 36, 48), 0.5))
+    info, pts, M, G = st.frame(1)
+    s = 3
+    u, v, sig = pts.u[s], pts.v[s], pts.sigma[s]
+    xn, yn = int(round(u)), int(round(v))
+    r2min = (xn - u) ** 2 + (yn - v) ** 2
+    assert r2min > 0.01          # off-pixel: the count-normalised peak is below 1
+    for x, y in ((10, 20), (xn, yn), (xn + 3, yn - 2)):
+        want = math.exp(-(((x - u) ** 2 + (y - v) ** 2) - r2min) / (2 * sig ** 2))
+        assert abs(M[y, x] - want) <= 1e-14
+    assert M.max() == 1.0 and M[yn, xn] == 1.0
+    assert info["map_max"] == 1.0 and (info["argmax_x"], info["argmax_y"]) == (xn, yn)
+    # depth 0.5 < d0 = 1: motion-guided depth equals the normalised map
+    np.testing.assert_array_equal(G, M)
+
+
+def test_max_normalised_is_a_rescaled_count_map():
+    """The two normalisations differ by one positive factor per frame; empty
+    frames stay all zero under both."""
+    from synth import small_stream
+    w = small_stream()
+    maps = {}
+    for norm in ("count", "max"):
+        p = O.Params(96, 72, window=8, smooth_len=15, mode=O.MODE_ACCEL, normalize=norm)
+        st = run(w.poses[:24], p, K=w.K() * np.array([0.3, 0.3, 0.3, 0.3]),
+                 depth=np.full((24, 72, 96), 3.0))
+        maps[norm] = [st.frame(n) for n in (0, 1, 20, 23)]
+    for (ic, _, Mc, Gc), (im, _, Mm, Gm) in zip(maps["count"], maps["max"]):
+        assert ic["n_valid"] == im["n_valid"]
+        if ic["n_valid"] == 0:
+            assert not Mc.any() and not Mm.any() and im["map_max"] == 0.0
+            continue
+        c = Mc.max()
+        assert 0.0 < c <= 1.0 and Mm.max() == 1.0
+        np.testing.assert_allclose(Mm * c, Mc, rtol=1e-15, atol=0)
+        np.testing.assert_allclose(Gm * c, Gc, rtol=1e-15, atol=0)
+        assert (im["argmax_x"], im["argmax_y"]) == (ic["argmax_x"], ic["argmax_y"])
+    assert any(i["n_valid"] > 0 for i, *_ in maps["max"])
+    assert any(i["n_valid"] == 0 for i, *_ in maps["max"])
+
+
 def test_brute_force_tiny_two_points():
     """4x3 map from two hand-placed points with sigma = 1 (values by hand)."""
     pts = O.FramePoints(0, 0, np.array([0.0, 3.0]), np.array([0.0, 2.0]),
