@@ -40,6 +40,9 @@ MAP_SRC = [os.path.join(ROOT, "paper_2601_07154_gb300", "csrc", f)
            for f in ("mf_map_kernel.cu", "mf_map_unit.cuh")]
 
 
+PIECE_FRAMES = max(1, min(64, (128 << 20) // (12 * WIDTH * HEIGHT)))  # library transfer piece
+
+
 def env_int(name, default):
     try:
         return int(os.environ.get(name, default))
@@ -239,6 +242,10 @@ def run_gpu(args):
     map_ms = (s1.map_kernel_ms - s0.map_kernel_ms) / max(1, s1.map_launches - s0.map_launches)
     ms, value = combine_ranks(torch, dist, ms, frames * args.steps, world, dev)
 
+    e2e = None
+    if rank == 0 and not args.no_e2e:
+        M = G = None
+        e2e = run_e2e(torch, mf, w, depth, dev, args)
     prec = None
     if rank == 0 and not args.no_precision:
         prec = run_precision(torch, mf, w, poses, depth, dev, args, value / world)
@@ -252,7 +259,8 @@ def run_gpu(args):
         pools32 = depth_pools(torch, dev, args.batch_frames, torch.float32)
         pools16 = {k: v.to(torch.bfloat16) for k, v in pools32.items()}
         batched = {"workload": "64 streams, resolutions 640x480..3840x2160, windows 8..32, "
-                               f"{args.batch_frames} frames per stream per step",
+                               f"{args.batch_frames} frames per stream per step, own depth "
+                               "planes per stream",
                    "engine_f32": run_batched(torch, mf, dev, args, pools32, torch.float32),
                    "engine_bf16": run_batched(torch, mf, dev, args, pools16, torch.bfloat16),
                    "plain_f32": run_batched(torch, mf, dev, args, pools32, torch.float32, plain=True)}
@@ -267,10 +275,6 @@ def run_gpu(args):
                       "plain_f32": run_served(torch, mf, dev, args, pools32, torch.float32,
                                               plain=True)}
         del pools32, pools16
-    e2e = None
-    if rank == 0 and not args.no_e2e:
-        M = G = None
-        e2e = run_e2e(torch, mf, w, depth, dev, args)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(w, args.cpu_seconds)
@@ -374,22 +378,36 @@ def run_e2e(torch, mf, w, depth_dev, dev, args):
     s = mf.MotionFocusStream(WIDTH, HEIGHT, window=WINDOW, smooth_len=SMOOTH, device=dev)
     h = s.handle
 
+    t_push = [0.0]
+
     def step():
+        t0 = time.perf_counter()
         mf.mf_reset_stream(h)
         mf.mf_push_frames(h, FR, poses_h, depth_h, Kh)
+        t_push[0] += time.perf_counter() - t0
         assert mf.mf_get_maps(h, FR, M_h, G_h, info_h, None) == FR
 
     for _ in range(2):
         step()
     n = max(3, args.e2e_steps)
+    t_push[0] = 0.0
+    laps = []
     t0 = time.perf_counter()
     for _ in range(n):
         step()
+        laps.append(time.perf_counter())
     dt = time.perf_counter() - t0
+    laps = np.diff([t0] + laps) * 1000.0
     s.close()
+    h2d = FR * 96 + FR * WIDTH * HEIGHT * 4
+    d2h = 2 * FR * WIDTH * HEIGHT * 4 + FR * 64
     return {"value": round(FR * n / dt, 2), "unit": "frames/s", "steps": n,
-            "h2d_bytes_per_step": FR * 96 + FR * WIDTH * HEIGHT * 4,
-            "d2h_bytes_per_step": 2 * FR * WIDTH * HEIGHT * 4 + FR * 64}
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "host_link_gbs": round((h2d + d2h) * n / dt / 1e9, 1),
+            "push_call_ms": round(1000 * t_push[0] / n, 2),
+            "step_ms_min_max": [round(float(laps.min()), 2), round(float(laps.max()), 2)],
+            "path": "pinned host depth/maps; uploads and downloads on two copy streams in "
+                    f"pieces of {PIECE_FRAMES} frames, overlapped with the map kernels"}
 
 
 # ------------------------------------------------- batched and served --
@@ -431,7 +449,9 @@ def run_batched(torch, mf, dev, args, pools, dtype, plain=False):
             M=torch.empty((F, sp.height, sp.width), dtype=dtype, device=dev),
             G=torch.empty((F, sp.height, sp.width), dtype=dtype, device=dev),
             info=torch.empty(F * 64, dtype=torch.uint8, device=dev),
-            depth=pools[(sp.width, sp.height)][:F]))
+            # every stream reads its own planes (a copy of the pool's), so
+            # depth reads come from HBM as they would for distinct cameras
+            depth=pools[(sp.width, sp.height)][:F].clone()))
     px = sum(s["w"] * s["h"] for s in streams) * F
     bpp = 3 * (4 if dtype == torch.float32 else 2)
     if plain:
@@ -683,7 +703,24 @@ def cpu_baseline(w, seconds):
     rate, dt = oracle_sample(w, frames, slice(0, HEIGHT))
     return {"value": round(rate, 4), "unit": "frames/s", "cores": 1, "kind": "oracle",
             "sample": f"{nframes} full 1920x1080 frames ({frames[0]}..{frames[-1]}) of the "
-                      f"900-frame workload, FP64 numpy oracle, {dt:.1f} s"}
+                      f"900-frame workload, FP64 numpy oracle, {dt:.1f} s",
+            "host": host_cpu()}
+
+
+def host_cpu():
+    """CPU of the host the oracle ran on (model name when the OS reports it)."""
+    import platform
+    model = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                k = ln.split(":")[0].strip().lower()
+                if k in ("model name", "cpu part", "hardware"):
+                    model = f"{platform.machine()} {ln.split(':', 1)[1].strip()}"
+                    break
+    except OSError:
+        pass
+    return {"model": model, "nproc": os.cpu_count(), "threads_used": 1}
 
 
 def run_reference(args):
@@ -725,7 +762,7 @@ def main():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

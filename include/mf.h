@@ -78,9 +78,11 @@ typedef enum {
 /* The normaliser Z of Eq. 7, which the paper leaves open:
  *   COUNT -- Z = number of valid points: M in [0, 1], 1 only where every
  *            point's Gaussian peaks (default);
- *   MAX   -- Z = the frame's largest point sum: every non-empty map is
- *            exactly 1 at its argmax (one extra in-place pass over M and G;
- *            mf_frame_info.map_max is then 1). */
+ *   MAX   -- Z = the frame's largest point sum: the map is exactly 1 at
+ *            its argmax (one extra in-place pass over M and G; map_max of
+ *            mf_frame_info is then 1).  A frame whose count-normalised
+ *            maximum is below 2^-20 (every point many sigma outside the
+ *            image) keeps its count-normalised maps and map_max. */
 typedef enum { MF_NORM_COUNT = 0, MF_NORM_MAX = 1 } mf_norm;
 
 /* mf_stream_desc.flags */
@@ -196,10 +198,12 @@ int mf_open_stream(const mf_stream_desc* d, mf_stream** out);
  * Emits frames overlap..n-1 (all n on the first push or in WORLD mode):
  * anchors them (BATCH_LOCAL, gravity-locked yaw + translation), appends
  * them to the pose history and computes their motion points on the GPU.
- * Host inputs are copied before the call returns; device inputs are read
- * asynchronously on the stream, pose buffers before any later push and
- * depth buffers when the frames are rendered by mf_get_maps -- keep them
- * unchanged until then.  A pose whose rotation is not orthonormal to 1e-6
+ * Host poses and pageable host depth are copied before the call returns.
+ * Pinned (page-locked) host depth is uploaded asynchronously by a copy
+ * engine, in pieces that the map kernels consume as they arrive; device
+ * inputs are read asynchronously on the stream, pose buffers before any
+ * later push and depth buffers when the frames are rendered by mf_get_maps.
+ * Keep pinned and device inputs unchanged until then.  A pose whose rotation is not orthonormal to 1e-6
  * (or not finite) makes its frame MF_FRAME_BAD_POSE and invalidates every
  * motion point whose fit uses it; a bad anchor makes the whole batch bad.
  * Errors: MF_ERR_INVALID_ARG (n < 1, n <= overlap on a later BATCH_LOCAL
@@ -223,7 +227,10 @@ int mf_push_frames(mf_stream* s, int32_t n, const double* poses_w2c_3x4,
  * If every non-NULL output is device memory the call only enqueues work on
  * the stream and returns; the results are ready once the stream reaches
  * that point (mf_sync).  If any output is host memory the call waits for
- * the copies; on MF_ERR_TIMEOUT the frames count as returned but copies into
+ * the copies.  Maps bound for host memory are rendered into a small device
+ * ring in pieces of a few frames, and each piece is downloaded by a copy
+ * engine while the next pieces render and the pinned-depth uploads of
+ * mf_push_frames run, so both transfer directions overlap; on MF_ERR_TIMEOUT the frames count as returned but copies into
  * the caller's host buffers may still be in flight: keep those buffers
  * alive until mf_sync or mf_close_stream returns.
  */

@@ -38,7 +38,7 @@ path's specification):
   Eq. 6 is applied literally (the sign of d_z is not used);
 * s_i = clamp(|d_i| / mean_valid |d|, s_lo, s_hi), spread sigma_i =
   sigma_rel * fx' * s_i, Z = number of valid points (or, optionally, the map's
-  largest value, so that the map peaks at 1);
+  largest value when that is at least 2^-20, so that the map peaks at 1);
 * intrinsics compensation (Section 1, "real camera intrinsics as physical
   constraints"): K given at a calibration resolution is rescaled to the map
   resolution with pixel centres at integer coordinates;
@@ -84,6 +84,12 @@ class Params:
     s_hi: float = 4.0
     depth_ref_m: float = 1.0
     normalize: str = "count"    # Z of Eq. 7: "count" (valid points) or "max" (map maximum)
+
+
+# Z = map maximum applies to maps whose count-normalised maximum is at least
+# this; a lower maximum means every point lies many sigma outside the image,
+# and such a map is left count-normalised.
+NORM_FLOOR = 2.0 ** -20
 
 
 # ---------------------------------------------------------------- Eqs. 2-3 --
@@ -391,7 +397,7 @@ class OracleStream:
         M = G = None
         if full_maps:
             M = focus_map(pts, p.width, p.height)
-            if p.normalize == "max" and M.max() > 0.0:
+            if p.normalize == "max" and M.max() >= NORM_FLOOR:
                 # Z = the map's largest point sum: the map peaks at exactly 1
                 M = M / M.max()
             if self.depth[n] is not None:

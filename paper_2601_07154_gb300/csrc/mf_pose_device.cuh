@@ -269,13 +269,16 @@ __device__ __forceinline__ void frame_points(const double* ring, const int32_t* 
 }
 
 // Divisor of a frame's maps under MF_NORM_MAX: the map maximum found by the
-// fused argmax, or 1 for an empty map (left as it is, all zeros).  Dividing
-// (rather than multiplying by a reciprocal) maps the maximum to exactly 1.
+// fused argmax when it is at least kNormFloor, else 1 (a frame whose motion
+// points all lie far outside the image keeps its near-zero count-normalised
+// maps).  Dividing, rather than multiplying by a reciprocal, maps the
+// maximum to exactly 1.
+constexpr float kNormFloor = 0x1p-20f;
 __device__ __forceinline__ float norm_divisor(const FrameRec* rec) {
   const unsigned long long key = rec->argmax_key;
   if (rec->n_valid <= 0 || key == 0ull) return 1.0f;
   const float mx = __uint_as_float((unsigned)(key >> 32));
-  return mx > 0.0f ? mx : 1.0f;
+  return mx >= kNormFloor ? mx : 1.0f;
 }
 
 __device__ __forceinline__ void finalize_frame(const FrameRec* rec, int width, mf_frame_info* out,
@@ -296,7 +299,7 @@ __device__ __forceinline__ void finalize_frame(const FrameRec* rec, int width, m
     o.argmax_x = (int)(idx % (unsigned)width);
     o.argmax_y = (int)(idx / (unsigned)width);
     o.map_max = __uint_as_float((unsigned)(key >> 32));
-    if (normalize == MF_NORM_MAX && o.map_max > 0.0f) o.map_max = 1.0f;
+    if (normalize == MF_NORM_MAX && o.map_max >= kNormFloor) o.map_max = 1.0f;
   } else {
     o.argmax_x = -1;
     o.argmax_y = -1;

@@ -152,7 +152,21 @@ struct Run {
   int count;
   const char* depth;   // plane of frame `first`, or NULL
   int stage_slots;     // staging slots this run holds (0: caller memory)
+  cudaEvent_t ready;   // upload of a staged run on the copy-in stream, or NULL
 };
+
+// Host-memory transfers are split into pieces of about this many bytes of
+// traffic (depth in + both maps out) so that uploads, map launches and
+// downloads of different pieces overlap.  Upload and download pieces hold
+// the same number of frames, so each map launch covers one upload.
+constexpr size_t kPieceBytes = 128u << 20;
+constexpr int kMaxPieceFrames = 64;
+constexpr int kOutSlots = 3;  // output staging pieces in flight
+
+int piece_frames(size_t frame_bytes) {
+  const size_t f = frame_bytes ? kPieceBytes / frame_bytes : kMaxPieceFrames;
+  return (int)std::max<size_t>(1, std::min<size_t>(f, kMaxPieceFrames));
+}
 
 struct TimerPair {
   cudaEvent_t a, b;
@@ -175,6 +189,7 @@ struct mf_stream {
   bool own_stream = false;
   double w[mf::kMaxHist] = {};
   size_t plane_in = 0, plane_out = 0;  // bytes per depth plane / map plane
+  int piece = 1;                       // frames per host-memory transfer piece
 
   double* ring = nullptr;
   int32_t* ring_bad = nullptr;
@@ -193,6 +208,13 @@ struct mf_stream {
   char* out_stage = nullptr;       // device staging of outputs bound for host
   size_t out_stage_bytes = 0;
   cudaEvent_t done_ev = nullptr;
+
+  // Copy engines for host memory: uploads run on st_in and downloads on
+  // st_out, so that both directions and the kernels on st overlap.
+  cudaStream_t st_in = nullptr, st_out = nullptr;
+  std::vector<cudaEvent_t> free_events;
+  cudaEvent_t slot_ev[kOutSlots] = {};  // download of each output slot's piece
+  bool slot_busy[kOutSlots] = {};
 
   int64_t emitted = 0, rendered = 0, pushes = 0, pushed_frames = 0;
   std::deque<Run> runs;
@@ -252,6 +274,46 @@ int grow_ring(mf_stream* s, int64_t need) {
   return MF_OK;
 }
 
+int take_event(mf_stream* s, cudaEvent_t* ev) {
+  if (!s->free_events.empty()) {
+    *ev = s->free_events.back();
+    s->free_events.pop_back();
+    return MF_OK;
+  }
+  MF_CUDA(cudaEventCreateWithFlags(ev, cudaEventDisableTiming), "event create");
+  return MF_OK;
+}
+
+// Makes `st` wait for a run's upload; the event goes back to the pool (a
+// wait enqueued on a stream keeps the state the event had at that time).
+int consume_ready(mf_stream* s, Run& r, cudaStream_t st) {
+  if (!r.ready) return MF_OK;
+  MF_CUDA(cudaStreamWaitEvent(st, r.ready, 0), "wait for upload");
+  s->free_events.push_back(r.ready);
+  r.ready = nullptr;
+  return MF_OK;
+}
+
+// st_b waits for all work enqueued so far on st_a.
+int order_after(mf_stream* s, cudaStream_t st_b, cudaStream_t st_a) {
+  cudaEvent_t ev;
+  int rc = take_event(s, &ev);
+  if (rc) return rc;
+  MF_CUDA(cudaEventRecord(ev, st_a), "event record");
+  MF_CUDA(cudaStreamWaitEvent(st_b, ev, 0), "stream wait");
+  s->free_events.push_back(ev);
+  return MF_OK;
+}
+
+int ensure_copy_streams(mf_stream* s) {
+  if (s->st_in) return MF_OK;
+  MF_CUDA(cudaStreamCreateWithFlags(&s->st_in, cudaStreamNonBlocking), "copy stream creation");
+  MF_CUDA(cudaStreamCreateWithFlags(&s->st_out, cudaStreamNonBlocking), "copy stream creation");
+  for (int k = 0; k < kOutSlots; ++k)
+    MF_CUDA(cudaEventCreateWithFlags(&s->slot_ev[k], cudaEventDisableTiming), "event create");
+  return MF_OK;
+}
+
 // Staging ring of depth planes for host-memory depth.  Grows (copying the
 // pending planes in order) when the pending planes plus `need` do not fit.
 int ensure_stage(mf_stream* s, int64_t need) {
@@ -259,10 +321,13 @@ int ensure_stage(mf_stream* s, int64_t need) {
   const int64_t slots = std::max<int64_t>(s->stage_used + need, 2 * s->stage_slots);
   char* buf = (char*)s->dalloc((size_t)slots * s->plane_in);
   if (!buf) return fail(MF_ERR_OOM, "depth staging allocation failed");
-  // move pending planes to slots 0..used-1 and repoint their runs
+  // move pending planes to slots 0..used-1 (after their uploads) and
+  // repoint their runs
   int64_t moved = 0;
   for (Run& r : s->runs) {
     if (r.stage_slots == 0) continue;
+    int rc = consume_ready(s, r, s->st);
+    if (rc) return rc;
     MF_CUDA(cudaMemcpyAsync(buf + (size_t)moved * s->plane_in, r.depth,
                             (size_t)r.count * s->plane_in, cudaMemcpyDeviceToDevice, s->st),
             "staging move");
@@ -270,6 +335,8 @@ int ensure_stage(mf_stream* s, int64_t need) {
     moved += r.count;
   }
   if (s->stage) {
+    // uploads of runs dropped by mf_reset_stream may still be in flight
+    if (s->st_in) MF_CUDA(cudaStreamSynchronize(s->st_in), "copy stream sync");
     MF_CUDA(cudaStreamSynchronize(s->st), "stream sync before freeing staging");
     s->dfree(s->stage, (size_t)s->stage_slots * s->plane_in);
   }
@@ -283,6 +350,7 @@ int ensure_stage(mf_stream* s, int64_t need) {
 int ensure_out_stage(mf_stream* s, size_t bytes) {
   if (bytes <= s->out_stage_bytes) return MF_OK;
   if (s->out_stage) {
+    if (s->st_out) MF_CUDA(cudaStreamSynchronize(s->st_out), "copy stream sync");
     MF_CUDA(cudaStreamSynchronize(s->st), "stream sync before freeing output staging");
     s->dfree(s->out_stage, s->out_stage_bytes);
     s->out_stage = nullptr;
@@ -340,6 +408,15 @@ int timer_pair(mf_stream* s, TimerPair* out) {
 
 void destroy(mf_stream* s) {
   if (s->st) cudaStreamSynchronize(s->st);
+  if (s->st_in) cudaStreamSynchronize(s->st_in);
+  if (s->st_out) cudaStreamSynchronize(s->st_out);
+  for (Run& r : s->runs)
+    if (r.ready) cudaEventDestroy(r.ready);
+  for (cudaEvent_t ev : s->free_events) cudaEventDestroy(ev);
+  for (int k = 0; k < kOutSlots; ++k)
+    if (s->slot_ev[k]) cudaEventDestroy(s->slot_ev[k]);
+  if (s->st_in) cudaStreamDestroy(s->st_in);
+  if (s->st_out) cudaStreamDestroy(s->st_out);
   collect_timers(s);
   for (TimerPair& t : s->free_timers) {
     cudaEventDestroy(t.a);
@@ -448,6 +525,7 @@ int mf_open_stream(const mf_stream_desc* d, mf_stream** out) {
   }
   s->plane_in = (size_t)d->width * d->height * dtype_size(d->depth_dtype);
   s->plane_out = (size_t)d->width * d->height * dtype_size(d->map_dtype);
+  s->piece = piece_frames(s->plane_in + 2 * s->plane_out);
   if (d->cuda_stream) {
     s->st = (cudaStream_t)d->cuda_stream;
   } else {
@@ -533,25 +611,36 @@ int mf_push_frames(mf_stream* s, int32_t n, const double* poses, const void* dep
   if (depth) {
     const char* dsrc = static_cast<const char*>(depth) + (size_t)O * s->plane_in;
     if (is_device_ptr(depth)) {
-      new_runs.push_back(Run{s->emitted, n_emit, dsrc, 0});
+      new_runs.push_back(Run{s->emitted, n_emit, dsrc, 0, nullptr});
     } else {
       rc = ensure_stage(s, n_emit);
       if (rc) return rc;
+      rc = ensure_copy_streams(s);
+      if (rc) return rc;
+      // A staging slot is reused only after the map kernels that read its
+      // previous plane: the uploads start after the work already on st.
+      rc = order_after(s, s->st_in, s->st);
+      if (rc) return rc;
+      const int piece = s->piece;
       int64_t done = 0;
       while (done < n_emit) {
         const int64_t slot = (s->stage_head + s->stage_used) % s->stage_slots;
-        const int64_t chunk = std::min<int64_t>(n_emit - done, s->stage_slots - slot);
+        const int64_t chunk = std::min<int64_t>({n_emit - done, s->stage_slots - slot, (int64_t)piece});
         char* dst = s->stage + (size_t)slot * s->plane_in;
         MF_CUDA(cudaMemcpyAsync(dst, dsrc + (size_t)done * s->plane_in,
-                                (size_t)chunk * s->plane_in, cudaMemcpyHostToDevice, s->st),
+                                (size_t)chunk * s->plane_in, cudaMemcpyHostToDevice, s->st_in),
                 "depth upload");
-        new_runs.push_back(Run{s->emitted + done, (int)chunk, dst, (int)chunk});
+        cudaEvent_t ev;
+        rc = take_event(s, &ev);
+        if (rc) return rc;
+        MF_CUDA(cudaEventRecord(ev, s->st_in), "event record");
+        new_runs.push_back(Run{s->emitted + done, (int)chunk, dst, (int)chunk, ev});
         s->stage_used += chunk;
         done += chunk;
       }
     }
   } else {
-    new_runs.push_back(Run{s->emitted, n_emit, nullptr, 0});
+    new_runs.push_back(Run{s->emitted, n_emit, nullptr, 0, nullptr});
   }
 
   mf::IngestParams ip{};
@@ -608,17 +697,26 @@ int mf_get_maps(mf_stream* s, int32_t max_frames, void* focus_map, void* guided_
   const bool g_host = guided_depth && !is_device_ptr(guided_depth);
   const bool i_host = info && !is_device_ptr(info);
   const bool p_host = points && !is_device_ptr(points);
-  const size_t maps_bytes = (size_t)take * s->plane_out;
+  const bool maps_host = m_host || g_host;
+  // Maps bound for host memory are rendered in pieces into a ring of
+  // kOutSlots staging pieces; each piece's download on st_out overlaps the
+  // next pieces' kernels and the uploads on st_in.
+  const int piece = maps_host ? s->piece : (int)take;
+  const size_t map_stage_bytes = maps_host ? (size_t)kOutSlots * piece * s->plane_out : 0;
   const size_t info_bytes = (size_t)take * sizeof(mf_frame_info);
   const size_t pts_bytes = (size_t)take * s->d.window * sizeof(mf_motion_point);
   auto round256 = [](size_t b) { return (b + 255) / 256 * 256; };
   size_t need = 0;
-  if (m_host) need += round256(maps_bytes);
-  if (g_host) need += round256(maps_bytes);
+  if (m_host) need += round256(map_stage_bytes);
+  if (g_host) need += round256(map_stage_bytes);
   if (i_host) need += round256(info_bytes);
   if (p_host) need += round256(pts_bytes);
   int rc = ensure_out_stage(s, need);
   if (rc) return rc;
+  if (maps_host || i_host || p_host) {
+    rc = ensure_copy_streams(s);
+    if (rc) return rc;
+  }
   char* cur = s->out_stage;
   auto place = [&](bool host, void* user, size_t bytes) -> char* {
     if (!user) return nullptr;
@@ -627,19 +725,61 @@ int mf_get_maps(mf_stream* s, int32_t max_frames, void* focus_map, void* guided_
     cur += round256(bytes);
     return p;
   };
-  char* Md = place(m_host, focus_map, maps_bytes);
-  char* Gd = place(g_host, guided_depth, maps_bytes);
+  char* Mst = place(m_host, focus_map, map_stage_bytes);
+  char* Gst = place(g_host, guided_depth, map_stage_bytes);
   char* Id = place(i_host, info, info_bytes);
   char* Pd = place(p_host, points, pts_bytes);
 
-  // one map launch per contiguous depth run
+  // Download of one rendered piece (host maps only), issued one piece late
+  // so that a synchronous copy into pageable memory still overlaps the next
+  // piece's kernel.
+  struct Piece {
+    int slot;
+    int64_t done;
+    int cnt;
+  };
+  Piece pending{-1, 0, 0};
+  auto download = [&](const Piece& q) -> int {
+    cudaEvent_t ev;
+    int r2 = take_event(s, &ev);
+    if (r2) return r2;
+    MF_CUDA(cudaEventRecord(ev, s->st), "event record");
+    MF_CUDA(cudaStreamWaitEvent(s->st_out, ev, 0), "stream wait");
+    s->free_events.push_back(ev);
+    const size_t off = (size_t)q.slot * piece * s->plane_out;
+    const size_t bytes = (size_t)q.cnt * s->plane_out;
+    if (m_host)
+      MF_CUDA(cudaMemcpyAsync(static_cast<char*>(focus_map) + (size_t)q.done * s->plane_out,
+                              Mst + off, bytes, cudaMemcpyDeviceToHost, s->st_out), "D2H");
+    if (g_host)
+      MF_CUDA(cudaMemcpyAsync(static_cast<char*>(guided_depth) + (size_t)q.done * s->plane_out,
+                              Gst + off, bytes, cudaMemcpyDeviceToHost, s->st_out), "D2H");
+    MF_CUDA(cudaEventRecord(s->slot_ev[q.slot], s->st_out), "event record");
+    s->slot_busy[q.slot] = true;
+    return MF_OK;
+  };
+
+  // one map launch per contiguous depth run (per piece for host maps)
   int64_t f = s->rendered;
   int64_t done = 0;
+  int pieces = 0;
   const bool timed = (s->d.flags & MF_FLAG_TIME_KERNELS) != 0;
   while (done < take) {
     Run& r = s->runs.front();
     const int64_t skip = f - r.first;
-    const int cnt = (int)std::min<int64_t>(r.count - skip, take - done);
+    const int cnt = (int)std::min<int64_t>({r.count - skip, take - done, (int64_t)piece});
+    rc = consume_ready(s, r, s->st);
+    if (rc) return rc;
+    const int slot = pieces % kOutSlots;
+    if (maps_host && s->slot_busy[slot])
+      MF_CUDA(cudaStreamWaitEvent(s->st, s->slot_ev[slot], 0), "wait for output slot");
+    auto target = [&](bool host, char* stage, void* user) -> char* {
+      if (!user) return nullptr;
+      if (host) return stage + (size_t)slot * piece * s->plane_out;
+      return static_cast<char*>(user) + (size_t)done * s->plane_out;
+    };
+    char* Mp = target(m_host, Mst, focus_map);
+    char* Gp = target(g_host, Gst, guided_depth);
     mf::MapParams mp{};
     mp.recs = s->recs;
     mp.rec_mask = s->rec_cap - 1;
@@ -651,8 +791,8 @@ int mf_get_maps(mf_stream* s, int32_t max_frames, void* focus_map, void* guided_
     mp.tiles_x = (s->d.width + mf::kTileW - 1) / mf::kTileW;
     mp.tiles_y = (s->d.height + mp.tile_h - 1) / mp.tile_h;
     mp.depth = r.depth ? r.depth + (size_t)skip * s->plane_in : nullptr;
-    mp.M = Md ? Md + (size_t)done * s->plane_out : nullptr;
-    mp.G = Gd ? Gd + (size_t)done * s->plane_out : nullptr;
+    mp.M = Mp;
+    mp.G = Gp;
     mp.d0 = (float)s->d.depth_ref_m;
     TimerPair tp{};
     if (timed) {
@@ -666,6 +806,25 @@ int mf_get_maps(mf_stream* s, int32_t max_frames, void* focus_map, void* guided_
       MF_CUDA(cudaEventRecord(tp.b, s->st), "event record");
       s->timers.push_back(tp);
     }
+    if (s->d.normalize == MF_NORM_MAX) {
+      mf::NormalizeParams np{};
+      np.recs = s->recs;
+      np.rec_mask = s->rec_cap - 1;
+      np.f0 = f;
+      np.n_frames = cnt;
+      np.plane = (int64_t)s->d.width * s->d.height;
+      np.M = Mp;
+      np.G = Gp;
+      MF_CUDA(mf::launch_normalize(np, s->d.map_dtype, s->st, &s->launches), "normalize launch");
+    }
+    if (maps_host) {
+      if (pending.slot >= 0) {
+        rc = download(pending);
+        if (rc) return rc;
+      }
+      pending = Piece{slot, done, cnt};
+    }
+    ++pieces;
     f += cnt;
     done += cnt;
     if (skip + cnt == r.count) {
@@ -676,16 +835,9 @@ int mf_get_maps(mf_stream* s, int32_t max_frames, void* focus_map, void* guided_
       s->runs.pop_front();
     }
   }
-  if (s->d.normalize == MF_NORM_MAX) {
-    mf::NormalizeParams np{};
-    np.recs = s->recs;
-    np.rec_mask = s->rec_cap - 1;
-    np.f0 = s->rendered;
-    np.n_frames = (int)take;
-    np.plane = (int64_t)s->d.width * s->d.height;
-    np.M = Md;
-    np.G = Gd;
-    MF_CUDA(mf::launch_normalize(np, s->d.map_dtype, s->st, &s->launches), "normalize launch");
+  if (pending.slot >= 0) {
+    rc = download(pending);
+    if (rc) return rc;
   }
   mf::FinalizeParams fp{};
   fp.recs = s->recs;
@@ -701,13 +853,19 @@ int mf_get_maps(mf_stream* s, int32_t max_frames, void* focus_map, void* guided_
   s->rendered += take;
   *n_out = (int32_t)take;
 
-  if (m_host || g_host || i_host || p_host) {
-    if (m_host)
-      MF_CUDA(cudaMemcpyAsync(focus_map, Md, maps_bytes, cudaMemcpyDeviceToHost, s->st), "D2H");
-    if (g_host)
-      MF_CUDA(cudaMemcpyAsync(guided_depth, Gd, maps_bytes, cudaMemcpyDeviceToHost, s->st), "D2H");
-    if (i_host) MF_CUDA(cudaMemcpyAsync(info, Id, info_bytes, cudaMemcpyDeviceToHost, s->st), "D2H");
-    if (p_host) MF_CUDA(cudaMemcpyAsync(points, Pd, pts_bytes, cudaMemcpyDeviceToHost, s->st), "D2H");
+  if (maps_host || i_host || p_host) {
+    if (i_host || p_host) {
+      rc = order_after(s, s->st_out, s->st);
+      if (rc) return rc;
+      if (i_host)
+        MF_CUDA(cudaMemcpyAsync(info, Id, info_bytes, cudaMemcpyDeviceToHost, s->st_out), "D2H");
+      if (p_host)
+        MF_CUDA(cudaMemcpyAsync(points, Pd, pts_bytes, cudaMemcpyDeviceToHost, s->st_out), "D2H");
+    }
+    // Later work on st (and mf_sync) comes after the downloads.
+    rc = order_after(s, s->st, s->st_out);
+    if (rc) return rc;
+    for (int k = 0; k < kOutSlots; ++k) s->slot_busy[k] = false;
     MF_CUDA(cudaEventRecord(s->done_ev, s->st), "event record");
     return wait_event(s->done_ev, timeout_ns);
   }
@@ -732,6 +890,8 @@ int mf_reset_stream(mf_stream* s) {
   // Host bookkeeping only: every kernel and copy already enqueued reads and
   // writes library memory in stream order before anything enqueued later.
   s->emitted = s->rendered = s->pushes = 0;
+  for (Run& r : s->runs)
+    if (r.ready) s->free_events.push_back(r.ready);
   s->runs.clear();
   s->stage_head = s->stage_used = 0;
   return MF_OK;

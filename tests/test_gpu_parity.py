@@ -194,15 +194,26 @@ def test_max_normalised_maps(mf, mode, storage):
     cst = O.OracleStream(cref)
     cst.push(w.poses, w.depth_stack(0, 64), w.K())
     intr = O.compensated_intrinsics(w.K(), ref.p)
-    nonempty = 0
+    normalised = kept = ambiguous = 0
     for n in range(ref.n_emitted):
         rinfo, rp, Mr, Gr = ref.frame(n)
         parity.check_frame(info[n], pts[n], rinfo, rp, intr, where=f"frame {n}")
         if rinfo["n_valid"] == 0:
             assert not M[n].any() and not G[n].any() and info[n]["map_max"] == 0.0
             continue
-        nonempty += 1
-        mx = cst.frame(n)[2].max()            # the divisor, from the count map
+        mx = cst.frame(n)[2].max()            # the count map's maximum
+        # each side compares its own maximum with the floor: inside the band
+        # where FP32 and FP64 maxima may fall on opposite sides, both are valid
+        if abs(mx - O.NORM_FLOOR) <= 4 * parity.MAP_RTOL * O.NORM_FLOOR:
+            ambiguous += 1
+            continue
+        if mx < O.NORM_FLOOR:                 # left count-normalised
+            kept += 1
+            parity.check_map(M[n], Mr, storage, f"M frame {n}")
+            parity.check_map(G[n], Gr, storage, f"G frame {n}")
+            assert abs(float(info[n]["map_max"]) - mx) <= parity.MAP_RTOL * mx + parity.MAP_ATOL
+            continue
+        normalised += 1
         parity.check_map(M[n], Mr, storage, f"M frame {n}", divisor=mx)
         parity.check_map(G[n], Gr, storage, f"G frame {n}", divisor=mx)
         assert info[n]["map_max"] == 1.0
@@ -210,7 +221,9 @@ def test_max_normalised_maps(mf, mode, storage):
         assert Mr[y, x] >= 1.0 - 4 * parity.MAP_RTOL
         if storage == "f32":
             assert M[n][y, x] == 1.0 and M[n].max() == 1.0
-    assert nonempty > 40
+    print(f"\nNORM_MAX {mode} {storage}: normalised {normalised}, kept {kept}, "
+          f"ambiguous {ambiguous}")
+    assert normalised > 10 and ambiguous <= 1
 
 
 # ------------------------------------------------------------ edge cases --
@@ -248,6 +261,97 @@ def test_host_pointers_match_device_pointers(mf):
     b = run_both(mf, w.poses, d, w.K(), 320, 240, mode="heading", on_host=True)
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
     assert np.array_equal(a[2], b[2]) and np.array_equal(a[3], b[3])
+
+
+def _transfer_case(mf, storage="f32", normalize="count", n=100, width=640, height=480):
+    """Poses, depth and intrinsics of a 640x480 heading stream (points in view)."""
+    poses = _accelerating_walk(n, width=width)
+    rng = np.random.default_rng(7)
+    depth = rng.uniform(0.2, 5.0, (n, height, width)).astype(np.float32)
+    depth[:, :3, :] = 0.0
+    K = np.array([0.8 * width, 0.8 * width, (width - 1) / 2, (height - 1) / 2])
+    return poses, torch.from_numpy(depth).to(TDT[storage]), K
+
+
+def _render(mf, poses, depth, K, pushes, gets, storage="f32", normalize="count", where="device",
+            reset_after_first=False):
+    """Push/get through the C ABI with inputs and outputs in `where` memory:
+    "device", "pinned" (page-locked host) or "pageable" (plain host)."""
+    dev = torch.device("cuda", 0)
+    dt = TDT[storage]
+    n, height, width = depth.shape
+    s = mf.MotionFocusStream(width, height, window=8, smooth_len=7, mode="heading",
+                             depth_dtype=dt, map_dtype=dt, device=dev, normalize=normalize)
+    if where == "device":
+        D = depth.to(dev)
+        P = torch.from_numpy(poses).to(dev)
+        M = torch.empty((n, height, width), dtype=dt, device=dev)
+        info = torch.empty(n * 64, dtype=torch.uint8, device=dev)
+    else:
+        pin = where == "pinned"
+        D = depth.clone().pin_memory() if pin else depth.clone()
+        P = np.ascontiguousarray(poses)
+        M = torch.empty((n, height, width), dtype=dt, pin_memory=pin)
+        info = torch.empty(n * 64, dtype=torch.uint8, pin_memory=pin)
+    G = torch.empty_like(M)
+    if reset_after_first:
+        lo, hi = pushes[0]
+        mf._mf.mf_push_frames(s.handle, hi - lo, P[lo:hi], D[lo:hi], K)
+        mf._mf.mf_reset_stream(s.handle)
+    done = 0
+    gi = iter(gets)
+    for lo, hi in pushes:
+        mf._mf.mf_push_frames(s.handle, hi - lo, P[lo:hi], D[lo:hi], K)
+        want = next(gi, None)
+        if want:
+            got = mf._mf.mf_get_maps(s.handle, want, M[done:], G[done:], info[done * 64:], None)
+            assert got == want
+            done += got
+    while done < n - 0:
+        got = mf._mf.mf_get_maps(s.handle, n - done, M[done:], G[done:], info[done * 64:], None)
+        if got == 0:
+            break
+        done += got
+    torch.cuda.synchronize()
+    s.close()
+    return (M.float().cpu().numpy(), G.float().cpu().numpy(),
+            info.cpu().numpy().view(mf._mf.FRAME_INFO_DTYPE), done)
+
+
+@pytest.mark.parametrize("storage,normalize", [("f32", "count"), ("bf16", "max")])
+def test_host_transfers_in_pieces_match_device_path(mf, storage, normalize):
+    """Pinned and pageable host inputs and outputs go through upload pieces,
+    a ring of output pieces and two copy streams; every output must equal the
+    all-device path bit for bit.  640x480 gives 34-frame pieces; the pushes
+    and gets below cut across them, wrap and grow the depth staging ring and
+    reuse the output ring many times."""
+    poses, depth, K = _transfer_case(mf, storage)
+    ref = _render(mf, poses, depth, K, [(0, 100)], [], storage, normalize, "device")
+    assert ref[3] == 100 and ref[2]["n_valid"].sum() > 400
+    cases = [
+        ("pinned", [(0, 100)], [45, 30]),
+        ("pinned", [(0, 50), (50, 100)], [45, 0]),
+        ("pinned", [(0, 20), (20, 90), (90, 100)], [7, 70, 0]),
+        ("pageable", [(0, 60), (60, 100)], [33, 0]),
+    ]
+    for where, pushes, gets in cases:
+        got = _render(mf, poses, depth, K, pushes, gets, storage, normalize, where)
+        assert got[3] == 100, (where, pushes)
+        for a, b, name in zip(ref[:3], got[:3], ("M", "G", "info")):
+            assert np.array_equal(a, b), (where, pushes, gets, name)
+
+
+def test_reset_with_uploads_in_flight(mf):
+    """A reset drops pending pinned uploads; the next pushes reuse the
+    staging ring (after growing it) without reading stale planes."""
+    poses, depth, K = _transfer_case(mf)
+    ref = _render(mf, poses, depth, K, [(0, 100)], [], where="device")
+    got = _render(mf, poses, depth, K, [(0, 30), (30, 100)], [0], where="pinned",
+                  reset_after_first=True)
+    # the dropped push held frames 0..29; after the reset frames restart at 0
+    assert got[3] == 100
+    for a, b in zip(ref[:3], got[:3]):
+        assert np.array_equal(a, b)
 
 
 def test_split_pushes_and_partial_gets(mf):

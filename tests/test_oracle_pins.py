@@ -246,6 +246,35 @@ def test_max_normalised_single_point_closed_form():
     np.testing.assert_array_equal(G, M)
 
 
+@pytest.mark.parametrize("u_out,normalised", [(-15.0, True), (-27.0, False)])
+def test_max_normalisation_floor(u_out, normalised):
+    """One point left of the image (yaw puts it at u = cx - fx tan(theta)):
+    15 px out its map still peaks at exp(-15^2 / (2 sigma^2)) >= 2^-20 and is
+    rescaled to 1; 27 px out the peak is below 2^-20 and the count map stays."""
+    fx, cx = 40.0, 23.5
+    th = math.atan((cx - u_out) / fx)
+    maps = {}
+    for norm in ("count", "max"):
+        p = O.Params(48, 36, window=4, smooth_len=2, mode=O.MODE_HEADING, normalize=norm)
+        st = run(_const_velocity(2, (0, 0, 0.05), rot=rot_y(th)), p, K=(fx, fx, cx, 17.5),
+                 depth=np.full((2, 36, 48), 2.0))
+        maps[norm] = st.frame(1)
+    (ic, pc, Mc, _), (im, _, Mm, _) = maps["count"], maps["max"]
+    assert ic["n_valid"] == 1 and abs(pc.u[3] - u_out) < 1e-9
+    # nearest pixel: column 0, and the lowest row closest to v (v = cy = 17.5)
+    dys = np.abs(np.arange(36) - pc.v[3])
+    y0 = int(np.argmin(dys))
+    peak = math.exp(-(u_out ** 2 + dys[y0] ** 2) / (2 * (0.1 * fx) ** 2))
+    assert abs(Mc.max() - peak) <= 1e-12 * peak
+    assert (ic["argmax_x"], ic["argmax_y"]) == (0, y0) == (0, 17)
+    if normalised:
+        assert Mc.max() >= O.NORM_FLOOR and Mm.max() == 1.0 and im["map_max"] == 1.0
+    else:
+        assert Mc.max() < O.NORM_FLOOR
+        np.testing.assert_array_equal(Mm, Mc)
+        assert im["map_max"] == ic["map_max"] == Mc.max()
+
+
 def test_max_normalised_is_a_rescaled_count_map():
     """The two normalisations differ by one positive factor per frame; empty
     frames stay all zero under both."""
@@ -263,6 +292,9 @@ def test_max_normalised_is_a_rescaled_count_map():
             assert not Mc.any() and not Mm.any() and im["map_max"] == 0.0
             continue
         c = Mc.max()
+        if c < O.NORM_FLOOR:
+            np.testing.assert_array_equal(Mm, Mc)
+            continue
         assert 0.0 < c <= 1.0 and Mm.max() == 1.0
         np.testing.assert_allclose(Mm * c, Mc, rtol=1e-15, atol=0)
         np.testing.assert_allclose(Gm * c, Gc, rtol=1e-15, atol=0)
