@@ -69,10 +69,13 @@ __device__ __forceinline__ float2 ffma2(float2 a, float b, float2 c) {
   return d;
 }
 
-// min(1, d0 / D) for finite D > 0, else 0: NaN and D <= 0 fail the
-// comparison, and D = +inf gives d0 * rcp(inf) = 0 by itself.
+// min(1, d0 / D) for finite D > 0, else 0, without a compare or select:
+// the saturated quotient is min(1, d0/D) for D > 0 and 0 for negative, NaN
+// and infinite D.  Subtracting the smallest denormal leaves every normal D
+// unchanged and moves D = +0 (and -0) below zero, so that "no depth" also
+// gives 0 instead of saturating +inf to 1.
 __device__ __forceinline__ float depth_weight(float D, float d0) {
-  return D > 0.0f ? fminf(1.0f, __fdividef(d0, D)) : 0.0f;
+  return __saturatef(__fdividef(d0, D - 0x1p-149f));
 }
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -316,16 +319,31 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
       for (int c = 0; c < CPT; ++c) gv[c] = m[c] * depth_weight(dv[c], ug.d0);
       Vec<TOut, CPT>::store(grow + off, 0, gv);
     }
-    float mm = m[0];
+  };
+  // Running maximum of this lane's pixels, one compare per row pair; ties go
+  // to the lower row, then to the lower column (the lowest linear index).
+  auto track = [&](const float2 (&a)[CPT / 2], const float2 (&b)[CPT / 2], bool two, int r) {
+    float ma = fmaxf(a[0].x, a[0].y), mb = fmaxf(b[0].x, b[0].y);
 #pragma unroll
-    for (int c = 1; c < CPT; ++c) mm = fmaxf(mm, m[c]);
+    for (int c = 1; c < CPT / 2; ++c) {
+      ma = fmaxf(ma, fmaxf(a[c].x, a[c].y));
+      mb = fmaxf(mb, fmaxf(b[c].x, b[c].y));
+    }
+    const float mm = two ? fmaxf(ma, mb) : ma;
     if (mm > best) {
       best = mm;
+      const bool first = ma == mm;
+      float m[CPT];
+#pragma unroll
+      for (int c = 0; c < CPT / 2; ++c) {
+        m[2 * c] = first ? a[c].x : b[c].x;
+        m[2 * c + 1] = first ? a[c].y : b[c].y;
+      }
       unsigned off = CPT - 1;
 #pragma unroll
       for (int c = CPT - 2; c >= 0; --c)
         if (m[c] == mm) off = c;
-      bidx = (unsigned)((y0 + r) * ug.width + xc) + off;
+      bidx = (unsigned)((y0 + r + (first ? 0 : 1)) * ug.width + xc) + off;
     }
   };
   // Rows r and r+1 per iteration: the ring slots of rows r-2 and r-1 were
@@ -356,6 +374,7 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
     if (!col_ok) continue;
     emit(a, d0v, r, off);
     if (two) emit(b, d1v, r + 1, off + ostride);
+    track(a, b, two, r);
   }
   cp_async_wait<0>();
   unsigned long long key =
