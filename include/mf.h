@@ -87,6 +87,13 @@ typedef enum { MF_NORM_COUNT = 0, MF_NORM_MAX = 1 } mf_norm;
 
 /* mf_stream_desc.flags */
 #define MF_FLAG_TIME_KERNELS 1u /* time each map-kernel launch with CUDA events */
+/* Map kernel choice.  Eq. 7 over a tile is a rank-N product of row and
+ * column factor tables, so it can run on the CUDA cores (one FMA per point
+ * and pixel; the default) or on the tensor cores (tcgen05 with TMEM
+ * accumulators, three TF32 products per FP32 term).  These flags force one
+ * of them (not both). */
+#define MF_FLAG_MAP_CUDA_CORES 8u
+#define MF_FLAG_MAP_TENSOR_CORES 16u
 
 /*
  * Stream descriptor.  Fill with mf_stream_desc_init() and override fields.

@@ -19,6 +19,8 @@ MF_MODE_ACCEL, MF_MODE_HEADING = 0, 1
 MF_POSES_WORLD, MF_POSES_BATCH_LOCAL = 0, 1
 MF_FRAME_OK, MF_FRAME_EMPTY, MF_FRAME_BAD_POSE = 0, 1, 2
 MF_FLAG_TIME_KERNELS = 1
+MF_FLAG_MAP_CUDA_CORES = 8
+MF_FLAG_MAP_TENSOR_CORES = 16
 MF_NORM_COUNT, MF_NORM_MAX = 0, 1
 (MF_OK, MF_ERR_INVALID_ARG, MF_ERR_INVALID_POSE, MF_ERR_OOM, MF_ERR_NOT_READY,
  MF_ERR_TIMEOUT, MF_ERR_CUDA, MF_ERR_ADMISSION, MF_ERR_NO_DEVICE) = range(9)

@@ -84,7 +84,13 @@ struct MapParams {
   void* M;                 // plane of frame f0 (may be NULL)
   void* G;                 // (may be NULL)
   float d0;
+  int path;                // kMapAuto, kMapCudaCores or kMapTensorCores
 };
+
+// Map kernel selection (MapParams::path).
+constexpr int kMapAuto = 0;
+constexpr int kMapCudaCores = 1;
+constexpr int kMapTensorCores = 2;
 
 struct FinalizeParams {
   const FrameRec* recs;
@@ -112,6 +118,9 @@ struct NormalizeParams {
 // the number of kernels launched.
 cudaError_t launch_ingest(const IngestParams& p, cudaStream_t st, int64_t* launches);
 cudaError_t launch_points(const PointsParams& p, cudaStream_t st, int64_t* launches);
+// Tensor-core map kernel (mf_map_tc.cu); any width, any plane alignment.
+cudaError_t launch_map_tc(const MapParams& p, int window, int depth_dtype, int map_dtype,
+                          cudaStream_t st, int64_t* launches);
 cudaError_t launch_map(const MapParams& p, int window, int in_dtype, int out_dtype,
                        cudaStream_t st, int64_t* launches);
 cudaError_t launch_finalize(const FinalizeParams& p, cudaStream_t st, int64_t* launches);
@@ -127,6 +136,7 @@ int map_tile_h(int width, int height, int window);
 // Host helpers defined in mf_stream.cpp.
 bool host_ls_weights(int K, int mode, double* w);
 int host_validate_desc(const mf_stream_desc* d);
+int host_map_path(uint32_t flags);
 int host_fail(int status, const char* what, cudaError_t e);
 void host_count_launches(int64_t n);
 

@@ -156,6 +156,7 @@ extern "C" int mf_render_noalloc(const mf_stream_desc* d, int32_t n_poses,
     mp.M = focus_map;
     mp.G = guided_depth;
     mp.d0 = (float)d->depth_ref_m;
+    mp.path = mf::host_map_path(d->flags);
     e = mf::launch_map(mp, d->window, d->depth_dtype, d->map_dtype, st, &launches);
   }
   if (e == cudaSuccess && d->normalize == MF_NORM_MAX) {

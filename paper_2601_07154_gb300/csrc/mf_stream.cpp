@@ -42,6 +42,12 @@ int fail(int status, const char* what, cudaError_t e = cudaSuccess) {
 
 size_t dtype_size(int dt) { return dt == MF_F32 ? 4 : 2; }
 
+int map_path(uint32_t flags) {
+  if (flags & MF_FLAG_MAP_TENSOR_CORES) return mf::kMapTensorCores;
+  if (flags & MF_FLAG_MAP_CUDA_CORES) return mf::kMapCudaCores;
+  return mf::kMapAuto;
+}
+
 int64_t pow2_at_least(int64_t v) {
   int64_t c = 1;
   while (c < v) c <<= 1;
@@ -465,6 +471,8 @@ int validate_desc(const mf_stream_desc* d) {
     return fail(MF_ERR_INVALID_ARG, "max_pending out of range");
   if (d->normalize != MF_NORM_COUNT && d->normalize != MF_NORM_MAX)
     return fail(MF_ERR_INVALID_ARG, "unknown normalisation");
+  if ((d->flags & MF_FLAG_MAP_CUDA_CORES) && (d->flags & MF_FLAG_MAP_TENSOR_CORES))
+    return fail(MF_ERR_INVALID_ARG, "choose one map kernel");
   if (!(d->sigma_rel > 0.0) || !(d->s_lo > 0.0) || !(d->s_hi >= d->s_lo) ||
       !(d->depth_ref_m > 0.0) || !std::isfinite(d->sigma_rel) || !std::isfinite(d->s_hi) ||
       !std::isfinite(d->depth_ref_m))
@@ -480,6 +488,7 @@ namespace mf {
 // Host helpers shared with the allocation-free entry point (mf_noalloc.cu).
 bool host_ls_weights(int K, int mode, double* w) { return ls_weights(K, mode, w); }
 int host_validate_desc(const mf_stream_desc* d) { return validate_desc(d); }
+int host_map_path(uint32_t flags) { return map_path(flags); }
 int host_fail(int status, const char* what, cudaError_t e) { return fail(status, what, e); }
 void host_count_launches(int64_t n) { g_launches.fetch_add(n); }
 }  // namespace mf
@@ -794,6 +803,7 @@ int mf_get_maps(mf_stream* s, int32_t max_frames, void* focus_map, void* guided_
     mp.M = Mp;
     mp.G = Gp;
     mp.d0 = (float)s->d.depth_ref_m;
+    mp.path = map_path(s->d.flags);
     TimerPair tp{};
     if (timed) {
       rc = timer_pair(s, &tp);

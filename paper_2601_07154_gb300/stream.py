@@ -11,6 +11,8 @@ from . import _mf
 
 _DT = {torch.float32: _mf.MF_F32, torch.bfloat16: _mf.MF_BF16, torch.float16: _mf.MF_F16}
 _NORMS = {"count": _mf.MF_NORM_COUNT, "max": _mf.MF_NORM_MAX}
+_MAP_KERNELS = {"auto": 0, "cuda_cores": _mf.MF_FLAG_MAP_CUDA_CORES,
+                "tensor_cores": _mf.MF_FLAG_MAP_TENSOR_CORES}
 _MODES = {"accel": _mf.MF_MODE_ACCEL, "heading": _mf.MF_MODE_HEADING}
 _FRAMES = {"world": _mf.MF_POSES_WORLD, "batch_local": _mf.MF_POSES_BATCH_LOCAL}
 
@@ -23,13 +25,15 @@ class MotionFocusStream:
     structured arrays (layouts of ``mf_frame_info`` / ``mf_motion_point``).
     ``normalize`` picks Z of Eq. 7: "count" (the number of valid points) or
     "max" (the frame's map maximum, so that every non-empty map peaks at 1).
+    ``map_kernel`` forces the CUDA-core ("cuda_cores") or the tensor-core
+    ("tensor_cores") map kernel; "auto" lets the library choose.
     """
 
     def __init__(self, width, height, window=8, smooth_len=15, mode="accel",
                  pose_frame="world", overlap=0, depth_dtype=torch.float32,
                  map_dtype=torch.float32, calib=None, sigma_rel=0.1, s_lo=0.25, s_hi=4.0,
                  depth_ref_m=1.0, max_pending=1024, device=None, cuda_stream=None,
-                 time_kernels=False, torch_allocator=True, normalize="count"):
+                 time_kernels=False, torch_allocator=True, normalize="count", map_kernel="auto"):
         self.device = torch.device(device) if device is not None else torch.device(
             "cuda", torch.cuda.current_device())
         self.width, self.height, self.window = int(width), int(height), int(window)
@@ -43,7 +47,8 @@ class MotionFocusStream:
                           mode=_MODES[mode], pose_frame=_FRAMES[pose_frame],
                           overlap=int(overlap), depth_dtype=_DT[depth_dtype],
                           map_dtype=_DT[map_dtype], max_pending=int(max_pending),
-                          flags=_mf.MF_FLAG_TIME_KERNELS if time_kernels else 0,
+                          flags=(_mf.MF_FLAG_TIME_KERNELS if time_kernels else 0)
+                          | _MAP_KERNELS[map_kernel],
                           normalize=_NORMS[normalize],
                           sigma_rel=sigma_rel, s_lo=s_lo, s_hi=s_hi, depth_ref_m=depth_ref_m,
                           # torch's default stream has handle 0, which the ABI

@@ -32,13 +32,13 @@ def _mode(name):
 
 def run_both(mf, poses, depth, K, width, height, window=8, smooth_len=15, mode="accel",
              storage="f32", pushes=None, pose_frame="world", overlap=0, calib=None,
-             on_host=False, get_chunks=None, normalize="count"):
+             on_host=False, get_chunks=None, normalize="count", map_kernel="auto"):
     """Run the same pushes through the GPU stream and the oracle."""
     dev = torch.device("cuda", 0)
     dt = TDT[storage]
     s = mf.MotionFocusStream(width, height, window=window, smooth_len=smooth_len, mode=mode,
                              pose_frame=pose_frame, overlap=overlap, depth_dtype=dt, map_dtype=dt,
-                             calib=calib, device=dev, normalize=normalize)
+                             calib=calib, device=dev, normalize=normalize, map_kernel=map_kernel)
     p = O.Params(width, height, window=window, smooth_len=smooth_len, mode=_mode(mode),
                  pose_frame=O.POSES_BATCH_LOCAL if pose_frame == "batch_local" else O.POSES_WORLD,
                  overlap=overlap, calib_width=calib[0] if calib else 0,
@@ -90,21 +90,26 @@ def compare_all(M, G, info, pts, ref, K, storage="f32", maps=True):
 
 
 # ---------------------------------------------------------------- configs --
+KERNELS = ["cuda_cores", "tensor_cores"]
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("mode", ["accel", "heading"])
-def test_small_stream_parity(mf, mode):
+def test_small_stream_parity(mf, mode, kernel):
     """320x240, 64 frames, window 8 (3 x 4 tiles with ragged right/bottom edges)."""
     w = small_stream()
     M, G, info, pts, ref = run_both(mf, w.poses, w.depth_stack(0, 64), w.K(), 320, 240,
-                                    window=8, smooth_len=15, mode=mode)
+                                    window=8, smooth_len=15, mode=mode, map_kernel=kernel)
     compare_all(M, G, info, pts, ref, w.K())
     assert info["n_valid"].sum() > 300
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("storage", ["bf16", "f16"])
-def test_small_stream_16bit_storage(mf, storage):
+def test_small_stream_16bit_storage(mf, storage, kernel):
     w = small_stream()
     M, G, info, pts, ref = run_both(mf, w.poses, w.depth_stack(0, 64), w.K(), 320, 240,
-                                    mode="heading", storage=storage)
+                                    mode="heading", storage=storage, map_kernel=kernel)
     compare_all(M, G, info, pts, ref, w.K(), storage=storage)
 
 
@@ -150,26 +155,30 @@ def _accelerating_walk(n, width=320, seed=0):
     return trajectory(cs, rs)
 
 
-@pytest.mark.parametrize("window,smooth_len", [(8, 3), (16, 15), (32, 33), (5, 7), (1, 3)])
-def test_windows_in_frame_accel(mf, window, smooth_len):
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("window,smooth_len", [(8, 3), (16, 15), (32, 33), (5, 7), (1, 3),
+                                               (24, 9)])
+def test_windows_in_frame_accel(mf, window, smooth_len, kernel):
     poses = _accelerating_walk(80)
     rng = np.random.default_rng(1)
     depth = rng.uniform(0.2, 5.0, (80, 240, 320)).astype(np.float32)
     K = np.array([260.0, 260.0, 160.0, 120.0])
     M, G, info, pts, ref = run_both(mf, poses, depth, K, 320, 240, window=window,
-                                    smooth_len=smooth_len, mode="accel")
+                                    smooth_len=smooth_len, mode="accel", map_kernel=kernel)
     compare_all(M, G, info, pts, ref, K)
     assert info["n_valid"][-1] == window and M[-1].max() > 0.05
 
 
-@pytest.mark.parametrize("width,height", [(333, 197), (130, 70), (4, 3), (1, 1), (129, 65)])
-def test_ragged_and_tiny_frames(mf, width, height):
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("width,height", [(333, 197), (130, 70), (4, 3), (1, 1), (129, 65),
+                                          (257, 129)])
+def test_ragged_and_tiny_frames(mf, width, height, kernel):
     poses = _accelerating_walk(30)
     rng = np.random.default_rng(2)
     depth = rng.uniform(0.2, 5.0, (30, height, width)).astype(np.float32)
     K = np.array([0.8 * width + 1, 0.8 * width + 1, (width - 1) / 2, (height - 1) / 2])
     M, G, info, pts, ref = run_both(mf, poses, depth, K, width, height, window=6,
-                                    smooth_len=5, mode="heading")
+                                    smooth_len=5, mode="heading", map_kernel=kernel)
     compare_all(M, G, info, pts, ref, K)
 
 
@@ -450,18 +459,21 @@ def test_streams_alone_and_interleaved_identical(mf):
 
 
 # ---------------------------------------------------------- full workload --
-def test_hd_stream_full_size_sampled(mf):
-    """1920x1080 x 900 frames, window 16, FP32: one push and one get of all
-    frames (the launch configuration the benchmark times).  Every frame's
-    integers, focus and motion points are checked; maps on 256 sampled
-    pixels per frame plus each frame's argmax."""
+@pytest.mark.parametrize("kernel,storage", [("cuda_cores", "f32"), ("tensor_cores", "f32"),
+                                            ("tensor_cores", "bf16")])
+def test_hd_stream_full_size_sampled(mf, kernel, storage):
+    """1920x1080 x 900 frames, window 16: one push and one get of all frames
+    (the launch configuration the benchmark times).  Every frame's integers,
+    focus and motion points are checked; maps on 256 sampled pixels per frame
+    plus each frame's argmax."""
     w = hd_stream()
     dev = torch.device("cuda", 0)
-    ring = torch.from_numpy(np.stack([w.depth(k) for k in range(w.ring)])).to(dev)
+    dt = TDT[storage]
+    ring = torch.from_numpy(np.stack([w.depth(k) for k in range(w.ring)])).to(dev).to(dt)
     idx = torch.tensor([k % w.ring for k in range(w.n_frames)], device=dev)
     depth = ring[idx].contiguous()
     s = mf.MotionFocusStream(w.width, w.height, window=w.window, smooth_len=w.smooth_len,
-                             device=dev)
+                             device=dev, depth_dtype=dt, map_dtype=dt, map_kernel=kernel)
     s.push(torch.from_numpy(w.poses).to(dev), depth, w.K())
     M, G, info, pts = s.get_maps()
     s.close()
@@ -480,18 +492,19 @@ def test_hd_stream_full_size_sampled(mf):
         rinfo, rp, _, _ = ref.frame(n, full_maps=False)
         parity.check_frame(info[n], pts[n], rinfo, rp, intr, where=f"frame {n}")
         Mr = O.focus_map(rp, w.width, w.height, xs, ys)
-        parity.check_map(Ms[n], Mr, where=f"M frame {n}")
+        parity.check_map(Ms[n], Mr, storage, where=f"M frame {n}")
         Gr = O.guided_depth(Mr, ringh[n % w.ring][ys, xs], 1.0)
-        parity.check_map(Gs[n], Gr, where=f"G frame {n}")
+        parity.check_map(Gs[n], Gr, storage, where=f"G frame {n}")
         if rinfo["n_valid"]:
             ax, ay = int(info[n]["argmax_x"]), int(info[n]["argmax_y"])
             m_at = O.focus_map(rp, w.width, w.height, np.array([ax]), np.array([ay]))[0]
             assert abs(float(info[n]["map_max"]) - m_at) <= 1e-5 * m_at + 1e-10
-            assert float(M[n, ay, ax]) == float(info[n]["map_max"])
+            if storage == "f32":
+                assert float(M[n, ay, ax]) == float(info[n]["map_max"])
     assert info["n_valid"].sum() > 5000
     # three whole frames against the full FP64 map (values and argmax)
     for n in (100, 451, 899):
         rinfo, rp, _, _ = ref.frame(n, full_maps=False)
         Mr = O.focus_map(rp, w.width, w.height)
-        parity.check_map(M[n].double().cpu().numpy(), Mr, where=f"full M frame {n}")
+        parity.check_map(M[n].double().cpu().numpy(), Mr, storage, where=f"full M frame {n}")
         parity.check_argmax(info[n], Mr, rinfo["n_valid"], where=f"argmax {n}")
