@@ -35,9 +35,11 @@ METRIC = "1080p frames/s & % HBM roofline; p99 frame latency, served vs plain, s
 WIDTH, HEIGHT, FRAMES, WINDOW, SMOOTH = 1920, 1080, 900, 16, 15
 BYTES_PER_PX = 12  # depth read + focus map write + guided depth write (FP32)
 FRAME_BYTES = WIDTH * HEIGHT * BYTES_PER_PX
-PROFILE = os.path.join(ROOT, "profiles", "map_kernel_1080p_f32.txt")
-MAP_SRC = [os.path.join(ROOT, "paper_2601_07154_gb300", "csrc", f)
-           for f in ("mf_map_kernel.cu", "mf_map_unit.cuh")]
+# committed ncu summary and the sources it was taken from, per map kernel
+PROFILES = {
+    "map_stream_kernel": ("map_kernel_1080p_f32.txt", ("mf_map_kernel.cu", "mf_map_unit.cuh")),
+    "map_tc_kernel": ("map_tc_kernel_1080p_f32.txt", ("mf_map_tc.cu", "mf_map_unit.cuh")),
+}
 
 
 PIECE_FRAMES = max(1, min(64, (128 << 20) // (12 * WIDTH * HEIGHT)))  # library transfer piece
@@ -67,27 +69,38 @@ def hbm_peak():
         return 6800.0, "fallback"
 
 
-def map_source_hash():
+def map_kernel_name(stats):
+    """Kernel of the stream's last map launch, by its CUDA function name."""
+    import paper_2601_07154_gb300 as mf
+    return {mf._mf.MF_FLAG_MAP_TENSOR_CORES: "map_tc_kernel",
+            mf._mf.MF_FLAG_MAP_CUDA_CORES: "map_stream_kernel"}.get(int(stats.last_map_kernel),
+                                                                   "unknown")
+
+
+def map_source_hash(kernel):
     h = hashlib.sha256()
-    for f in MAP_SRC:
-        if os.path.exists(f):
-            h.update(open(f, "rb").read())
+    for f in PROFILES[kernel][1]:
+        path = os.path.join(ROOT, "paper_2601_07154_gb300", "csrc", f)
+        if os.path.exists(path):
+            h.update(open(path, "rb").read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(frames):
-    """DRAM bytes per launch from the committed ncu summary, if it matches the source."""
+def profiled_traffic(frames, kernel):
+    """DRAM bytes per launch from the committed ncu summary of `kernel`, if
+    the summary was taken from the current sources."""
+    if kernel not in PROFILES:
+        return None
     try:
-        text = open(PROFILE).read()
+        text = open(os.path.join(ROOT, "profiles", PROFILES[kernel][0])).read()
     except OSError:
         return None
-    src_hash = map_source_hash()
     vals = {}
     for line in text.splitlines():
         if ":" in line:
             k, v = line.split(":", 1)
             vals[k.strip()] = v.strip()
-    if vals.get("source_sha256_16") != src_hash:
+    if vals.get("source_sha256_16") != map_source_hash(kernel):
         return None
     try:
         per_frame = float(vals["dram_bytes_per_frame"])
@@ -209,7 +222,7 @@ def run_gpu(args):
     info = torch.empty(frames * 64, dtype=torch.uint8, device=dev)
     stream = torch.cuda.Stream(dev)
     s = mf.MotionFocusStream(WIDTH, HEIGHT, window=WINDOW, smooth_len=SMOOTH, device=dev,
-                             cuda_stream=stream, time_kernels=True)
+                             cuda_stream=stream, time_kernels=True, map_kernel=args.map_kernel)
     h = s.handle
     Kh = np.ascontiguousarray(K)
 
@@ -290,9 +303,10 @@ def run_gpu(args):
             "config": workload_config(frames),
             "mpx_per_s": round(value * WIDTH * HEIGHT / 1e6, 1),
             "step_hbm_gbs": round(value / world * FRAME_BYTES / 1e9, 1),
-            "roofline": {"bound": "hbm", "kernel": "map_kernel", "achieved": round(achieved, 1),
+            "roofline": {"bound": "hbm", "kernel": map_kernel_name(s1), "achieved": round(achieved, 1),
                          "peak": peak, "peak_kind": kind, "unit": "GB/s",
-                         "frac": round(achieved / peak, 4), "traffic": profiled_traffic(frames),
+                         "frac": round(achieved / peak, 4),
+                         "traffic": profiled_traffic(frames, map_kernel_name(s1)),
                          "algorithmic_bytes_per_launch": frames * FRAME_BYTES,
                          "launch_ms": round(map_ms, 4)},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
@@ -768,6 +782,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip the HEADING / Z=max legs")
+    ap.add_argument("--map-kernel", default="auto", choices=["auto", "cuda_cores", "tensor_cores"],
+                    help="map kernel of the default line (auto: the library's choice)")
     ap.add_argument("--no-serving", action="store_true", help="skip the batched and served legs")
     ap.add_argument("--no-served", action="store_true", help="skip the served leg")
     ap.add_argument("--no-tune", action="store_true", help="engine legs use the plain tile height")

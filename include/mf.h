@@ -89,9 +89,11 @@ typedef enum { MF_NORM_COUNT = 0, MF_NORM_MAX = 1 } mf_norm;
 #define MF_FLAG_TIME_KERNELS 1u /* time each map-kernel launch with CUDA events */
 /* Map kernel choice.  Eq. 7 over a tile is a rank-N product of row and
  * column factor tables, so it can run on the CUDA cores (one FMA per point
- * and pixel; the default) or on the tensor cores (tcgen05 with TMEM
- * accumulators, three TF32 products per FP32 term).  These flags force one
- * of them (not both). */
+ * and pixel) or on the tensor cores (tcgen05 with TMEM accumulators, three
+ * TF32 products per FP32 term).  By default the library takes the faster
+ * one as measured on GB300: the tensor cores for FP32 maps with windows up
+ * to 16 points and for 16-bit maps with larger windows, the CUDA cores
+ * otherwise.  These flags force one of them (not both). */
 #define MF_FLAG_MAP_CUDA_CORES 8u
 #define MF_FLAG_MAP_TENSOR_CORES 16u
 
@@ -176,6 +178,9 @@ typedef struct {
   int64_t map_launches;      /* map-kernel launches timed (MF_FLAG_TIME_KERNELS) */
   double map_kernel_ms;      /* summed CUDA-event time of those launches */
   int64_t device_bytes;      /* device memory the stream holds */
+  uint32_t last_map_kernel;  /* MF_FLAG_MAP_CUDA_CORES or MF_FLAG_MAP_TENSOR_CORES:
+                                the kernel of the last map launch (0 before any) */
+  uint32_t reserved;
 } mf_stats;
 
 /* Fill *d with defaults (sigma_rel 0.1, s in [0.25, 4], d0 = 1 m, ACCEL,

@@ -66,7 +66,8 @@ class MFStats(ctypes.Structure):
         ("frames_pushed", ctypes.c_int64), ("frames_emitted", ctypes.c_int64),
         ("frames_rendered", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
         ("map_launches", ctypes.c_int64), ("map_kernel_ms", ctypes.c_double),
-        ("device_bytes", ctypes.c_int64),
+        ("device_bytes", ctypes.c_int64), ("last_map_kernel", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32),
     ]
 
 

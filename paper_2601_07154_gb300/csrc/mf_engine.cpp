@@ -749,13 +749,15 @@ int mf_engine_tick(mf_engine* e, int64_t* tick) {
     ENG_CUDA(cudaEventRecord(tb, e->st), "event");
     e->pending_timers.emplace_back(ta, tb);
   }
-  ENG_CUDA(cudaEventRecord(e->done[b], e->st), "event");
   {
     std::unique_ptr<TickRecord> rec(new TickRecord());
     rec->submit_ns.swap(e->frame_submit_ns);
     ENG_CUDA(cudaLaunchHostFunc(e->st, stamp_tick_done, rec.get()), "tick completion stamp");
     e->in_flight.push_back(std::move(rec));
   }
+  // recorded after the stamp: a tick that waits report as done has its
+  // completion time stamped too
+  ENG_CUDA(cudaEventRecord(e->done[b], e->st), "event");
   e->frame_submit_ns.clear();
   e->buf_tick[b] = t;
   ++e->ticks;

@@ -34,7 +34,7 @@ namespace {
 
 constexpr int kTcCols = 128;               // tile columns = MMA M = TMEM lanes
 constexpr int kTcRows = 64;                // tile rows = MMA N = TMEM columns
-constexpr int kTcKMax = 3 * kMaxPts;       // K' for 32 points
+constexpr int kTcKsMax = 2 * kMaxPts;      // stored K columns for 32 points
 constexpr int kTcThreads = 256;
 constexpr long long kTcWaitPolls = 1ll << 22;
 
@@ -118,26 +118,129 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 
 }  // namespace
 
+// Column factors of the kept points for one strip: A = [hi | lo], 2 kp
+// stored K columns.  Consecutive threads fill one core matrix (8 rows x 4
+// words), so a warp's stores are free of bank conflicts.
+__device__ __forceinline__ void build_cols(float* sA, const PointsSmem<kMaxPts>& P, int nk, int kp,
+                                           int gx0, int width) {
+  const int ks = 2 * kp;
+  for (int idx = threadIdx.x; idx < kTcCols * kp; idx += kTcThreads) {
+    const int i_lo = idx & 3, r_lo = (idx >> 2) & 7, g = idx >> 5;
+    const int kg = g % (kp >> 2), r_hi = g / (kp >> 2);
+    const int m = 8 * r_hi + r_lo, i = 4 * kg + i_lo;
+    const int x = gx0 + m;
+    float e = 0.0f;
+    if (i < nk && x < width) e = gauss_factor((float)x, P.uhi[i], P.ulo[i], P.chi[i], P.clo[i]);
+    float hi, lo;
+    split_tf32(e, hi, lo);
+    sA[operand_word(m, i, ks)] = hi;
+    sA[operand_word(m, kp + i, ks)] = lo;
+  }
+}
+
+// Row factors times 1/Z for one band: B = [hi | lo].
+__device__ __forceinline__ void build_rows(float* sB, const PointsSmem<kMaxPts>& P, int nk, int kp,
+                                           int y0, int rows, float inv_n) {
+  const int ks = 2 * kp;
+  for (int idx = threadIdx.x; idx < kTcRows * kp; idx += kTcThreads) {
+    const int i_lo = idx & 3, r_lo = (idx >> 2) & 7, g = idx >> 5;
+    const int kg = g % (kp >> 2), r_hi = g / (kp >> 2);
+    const int r = 8 * r_hi + r_lo, i = 4 * kg + i_lo;
+    float e = 0.0f;
+    if (i < nk && r < rows)
+      e = gauss_factor((float)(y0 + r), P.vhi[i], P.vlo[i], P.chi[i], P.clo[i]) * inv_n;
+    float hi, lo;
+    split_tf32(e, hi, lo);
+    sB[operand_word(r, i, ks)] = hi;
+    sB[operand_word(r, kp + i, ks)] = lo;
+  }
+}
+
+// One elected thread: D = A_hi B_hi + A_hi B_lo + A_lo B_hi into a TMEM
+// accumulator, as 3 kp/8 MMAs of K = 8, then a commit to the mbarrier.
+__device__ __forceinline__ void issue_mma(uint32_t d_tmem, const float* sA, const float* sB, int kp,
+                                          uint64_t* bar) {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t lbo = 128, sbo = (uint32_t)(2 * kp >> 2) * 128;
+  const uint32_t a0 = smem_addr(sA), b0 = smem_addr(sB);
+  int step = 0;
+  for (int j = 0; j < 3; ++j)
+    for (int t = 0; t < kp / 8; ++t, ++step) {
+      // blocks (A, B): (hi, hi), (hi, lo), (lo, hi)
+      const uint32_t ka = (uint32_t)((j == 2 ? (kp >> 2) : 0) + 2 * t);
+      const uint32_t kb = (uint32_t)((j == 1 ? (kp >> 2) : 0) + 2 * t);
+      const uint64_t ad = operand_desc(a0 + ka * 128u, lbo, sbo);
+      const uint64_t bd = operand_desc(b0 + kb * 128u, lbo, sbo);
+      asm volatile(
+          "{\n\t.reg .pred acc;\n\tsetp.ne.b32 acc, %4, 0;\n\t"
+          "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, acc;\n\t}" ::"r"(d_tmem),
+          "l"(ad), "l"(bd), "r"(kTcIdesc), "r"(step)
+          : "memory");
+    }
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_addr(bar))
+               : "memory");
+}
+
+// Requests a band's depth tile (64 rows x 128 columns) into shared memory.
+template <typename TIn, bool VEC>
+__device__ __forceinline__ void fetch_depth(TIn* sD, const TIn* dplane, int width, int gx0, int y0,
+                                            int rows) {
+  if (VEC) {
+    constexpr int kPerCopy = 16 / (int)sizeof(TIn);
+    constexpr int kCopiesPerRow = kTcCols / kPerCopy;
+    for (int c = threadIdx.x; c < kTcRows * kCopiesPerRow; c += kTcThreads) {
+      const int r = c / kCopiesPerRow, col = (c - r * kCopiesPerRow) * kPerCopy;
+      if (r < rows && gx0 + col < width)
+        cp_async<16>(sD + r * kTcCols + col, dplane + (size_t)(y0 + r) * width + gx0 + col);
+    }
+  } else {
+    for (int c = threadIdx.x; c < kTcRows * kTcCols; c += kTcThreads) {
+      const int r = c / kTcCols, col = c - r * kTcCols;
+      if (r < rows && gx0 + col < width) sD[c] = dplane[(size_t)(y0 + r) * width + gx0 + col];
+    }
+  }
+  cp_async_commit();
+}
+
+__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t phase) {
+  uint32_t done = 0;
+  for (long long it = 0; it < kTcWaitPolls && !done; ++it)
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(phase)
+        : "memory");
+  return done != 0;
+}
+
+// Software pipeline over the bands of a strip, two buffers deep: while the
+// epilogue of band b reads TMEM accumulator b%2 and depth tile b%2, the
+// depth copies and the MMAs of band b+1 run into the other buffers.
 template <typename TIn, typename TOut, bool VEC>
-__global__ void __launch_bounds__(kTcThreads, 2) map_tc_kernel(MapParams p, int strips, int kk_max) {
+__global__ void __launch_bounds__(kTcThreads, 2) map_tc_kernel(MapParams p, int strips, int ks_max) {
   extern __shared__ __align__(1024) unsigned char tc_smem[];
-  float* sA = reinterpret_cast<float*>(tc_smem);                 // [128][kk_max]
-  float* sB = sA + (size_t)kTcCols * kk_max;                     // [64][kk_max]
-  TIn* sD = reinterpret_cast<TIn*>(sB + (size_t)kTcRows * kk_max);  // [64][128] depth tile
+  float* sA = reinterpret_cast<float*>(tc_smem);  // [128][ks_max]
+  float* const sB0 = sA + (size_t)kTcCols * ks_max;
+  float* const sB1 = sA + (size_t)(kTcCols + kTcRows) * ks_max;
+  TIn* const sD0 = reinterpret_cast<TIn*>(sA + (size_t)(kTcCols + 2 * kTcRows) * ks_max);
+  TIn* const sD1 = sD0 + kTcRows * kTcCols;
   __shared__ PointsSmem<kMaxPts> P;
-  __shared__ __align__(8) uint64_t mma_bar;
+  __shared__ __align__(8) uint64_t mma_bar[2];
   __shared__ uint32_t tmem_slot;
   __shared__ int s_kept;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mma_bar)) : "memory");
+    for (int k = 0; k < 2; ++k)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mma_bar[k])) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_addr(&tmem_slot)),
-                 "r"(kTcRows)
+                 "r"(2 * kTcRows)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -145,14 +248,13 @@ __global__ void __launch_bounds__(kTcThreads, 2) map_tc_kernel(MapParams p, int 
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
-  uint32_t phase = 0;
+  uint32_t phase0 = 0u, phase1 = 0u;
 
   // epilogue role: TMEM lane quadrant q (32 columns), row half h (32 rows)
   const int q = warp & 3, h = warp >> 2;
   const size_t plane = (size_t)p.width * p.height;
   const int bands = (p.height + kTcRows - 1) / kTcRows;
   const int items = p.n_frames * strips;
-  constexpr int kPerCopy = 16 / (int)sizeof(TIn);  // elements per 16-byte copy
 
   for (int item = blockIdx.x; item < items; item += gridDim.x) {
     const int f = item / strips;
@@ -161,7 +263,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) map_tc_kernel(MapParams p, int 
     const FrameRec* rec = p.recs + ((p.f0 + f) & p.rec_mask);
     const int n = rec->n_valid;
     const float inv_n = rec->inv_n;
-    __syncthreads();  // the previous item is done with P, A, B and the depth tile
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();  // the previous item is done with every buffer
     if (warp == 0) {
       // points whose Gaussian can reach the strip (the CUDA-core kernel's
       // rule, over all rows of the frame); kept points keep their order
@@ -194,24 +297,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) map_tc_kernel(MapParams p, int 
     __syncthreads();
     const int nk = s_kept;
     const int kp = (nk + 7) & ~7;
-    const int kk = 3 * kp;
-    // A: column factors, [hi | hi | lo].  Consecutive threads fill one core
-    // matrix (8 rows x 4 words), so the stores are free of bank conflicts.
-    for (int idx = tid; idx < kTcCols * kp; idx += kTcThreads) {
-      const int i_lo = idx & 3, r_lo = (idx >> 2) & 7, g = idx >> 5;
-      const int kg = g % (kp >> 2), r_hi = g / (kp >> 2);
-      const int m = 8 * r_hi + r_lo, i = 4 * kg + i_lo;
-      const int x = gx0 + m;
-      float e = 0.0f;
-      if (i < nk && x < p.width) e = gauss_factor((float)x, P.uhi[i], P.ulo[i], P.chi[i], P.clo[i]);
-      float hi, lo;
-      split_tf32(e, hi, lo);
-      sA[operand_word(m, i, kk)] = hi;
-      sA[operand_word(m, kp + i, kk)] = hi;
-      sA[operand_word(m, 2 * kp + i, kk)] = lo;
-    }
 
-    // this thread's column and its running argmax over the strip
     const int x = gx0 + 32 * q + lane;
     const bool col_ok = x < p.width;
     float best = -1.0f;
@@ -221,85 +307,56 @@ __global__ void __launch_bounds__(kTcThreads, 2) map_tc_kernel(MapParams p, int 
     char* gplane = p.G ? static_cast<char*>(p.G) + (size_t)f * plane * sizeof(TOut) : nullptr;
     const bool want_depth = dplane && gplane && nk > 0;
 
+    if (nk > 0) {
+      // prologue: band 0 into buffers 0
+      build_cols(sA, P, nk, kp, gx0, p.width);
+      if (want_depth) fetch_depth<TIn, VEC>(sD0, dplane, p.width, gx0, 0, min(kTcRows, p.height));
+      build_rows(sB0, P, nk, kp, 0, min(kTcRows, p.height), inv_n);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (tid == 0) issue_mma(tmem, sA, sB0, kp, &mma_bar[0]);
+    }
+
     for (int b = 0; b < bands; ++b) {
+      const int cur = b & 1, nxt = cur ^ 1;
       const int y0 = b * kTcRows;
       const int rows = min(kTcRows, p.height - y0);
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncthreads();  // the previous band's epilogue is done with TMEM and the depth tile
-      if (want_depth) {
-        // the band's depth tile, in flight while B is built and multiplied
-        if (VEC) {
-          constexpr int kCopiesPerRow = kTcCols / kPerCopy;
-          for (int c = tid; c < kTcRows * kCopiesPerRow; c += kTcThreads) {
-            const int r = c / kCopiesPerRow, col = (c - r * kCopiesPerRow) * kPerCopy;
-            if (r < rows && gx0 + col < p.width)
-              cp_async<16>(sD + r * kTcCols + col, dplane + (size_t)(y0 + r) * p.width + gx0 + col);
-          }
-        } else {
-          for (int c = tid; c < kTcRows * kTcCols; c += kTcThreads) {
-            const int r = c / kTcCols, col = c - r * kTcCols;
-            if (r < rows && gx0 + col < p.width) sD[c] = dplane[(size_t)(y0 + r) * p.width + gx0 + col];
-          }
-        }
-        cp_async_commit();
-      }
       bool ok = true;
       if (nk > 0) {
-        // B: row factors times 1/Z, [hi | lo | hi], one core matrix per warp store
-        for (int idx = tid; idx < kTcRows * kp; idx += kTcThreads) {
-          const int i_lo = idx & 3, r_lo = (idx >> 2) & 7, g = idx >> 5;
-          const int kg = g % (kp >> 2), r_hi = g / (kp >> 2);
-          const int r = 8 * r_hi + r_lo, i = 4 * kg + i_lo;
-          float e = 0.0f;
-          if (i < nk && r < rows)
-            e = gauss_factor((float)(y0 + r), P.vhi[i], P.vlo[i], P.chi[i], P.clo[i]) * inv_n;
-          float hi, lo;
-          split_tf32(e, hi, lo);
-          sB[operand_word(r, i, kk)] = hi;
-          sB[operand_word(r, kp + i, kk)] = lo;
-          sB[operand_word(r, 2 * kp + i, kk)] = hi;
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();  // band b-1's epilogue is done with TMEM and depth buffers nxt
+        const bool more = b + 1 < bands;
+        if (more) {
+          const int y1 = y0 + kTcRows, rows1 = min(kTcRows, p.height - y1);
+          if (want_depth) fetch_depth<TIn, VEC>(nxt ? sD1 : sD0, dplane, p.width, gx0, y1, rows1);
+          build_rows(nxt ? sB1 : sB0, P, nk, kp, y1, rows1, inv_n);
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          __syncthreads();  // B of band b+1 written
+          if (tid == 0)
+            issue_mma(tmem + (uint32_t)(nxt * kTcRows), sA, nxt ? sB1 : sB0, kp, &mma_bar[nxt]);
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();  // operands written
-        if (tid == 0) {
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t lbo = 128, sbo = (uint32_t)(kk >> 2) * 128;
-          const uint32_t a0 = smem_addr(sA), b0 = smem_addr(sB);
-          for (int s = 0; s < kk / 8; ++s) {
-            const uint64_t ad = operand_desc(a0 + 256u * s, lbo, sbo);
-            const uint64_t bd = operand_desc(b0 + 256u * s, lbo, sbo);
-            asm volatile(
-                "{\n\t.reg .pred acc;\n\tsetp.ne.b32 acc, %4, 0;\n\t"
-                "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, acc;\n\t}" ::"r"(tmem),
-                "l"(ad), "l"(bd), "r"(kTcIdesc), "r"(s)
-                : "memory");
-          }
-          asm volatile(
-              "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                  smem_addr(&mma_bar))
-              : "memory");
+        if (want_depth) {
+          if (more)
+            cp_async_wait<1>();
+          else
+            cp_async_wait<0>();
         }
-        if (want_depth) cp_async_wait<0>();
-        __syncthreads();  // every thread's part of the depth tile has landed
-        uint32_t done = 0;
-        for (long long it = 0; it < kTcWaitPolls && !done; ++it)
-          asm volatile(
-              "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-              "selp.u32 %0, 1, 0, p;\n\t}"
-              : "=r"(done)
-              : "r"(smem_addr(&mma_bar)), "r"(phase)
-              : "memory");
-        phase ^= 1u;
-        ok = done != 0;
+        __syncthreads();  // every thread's part of depth tile b has landed
+        ok = wait_bar(&mma_bar[cur], cur ? phase1 : phase0);
+        if (cur)
+          phase1 ^= 1u;
+        else
+          phase0 ^= 1u;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       }
       // epilogue: rows y0 + 32h + 16c + j of column x
+      const TIn* dtile = cur ? sD1 : sD0;
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
         const int r0 = 32 * h + 16 * c;
         float acc[16];
         if (nk > 0) {
-          tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)r0, acc);
+          tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(cur * kTcRows + r0), acc);
         } else {
 #pragma unroll
           for (int j = 0; j < 16; ++j) acc[j] = 0.0f;
@@ -313,7 +370,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) map_tc_kernel(MapParams p, int 
           const size_t off = (size_t)(y0 + r0 + j) * p.width + x;
           if (mplane) Scalar<TOut>::store(mplane, off, m);
           if (gplane) {
-            const float dv = want_depth ? to_float(sD[(r0 + j) * kTcCols + 32 * q + lane]) : 0.0f;
+            const float dv = want_depth ? to_float(dtile[(r0 + j) * kTcCols + 32 * q + lane]) : 0.0f;
             Scalar<TOut>::store(gplane, off, m * depth_weight(dv, p.d0));
           }
           cmax = fmaxf(cmax, m);
@@ -340,14 +397,15 @@ __global__ void __launch_bounds__(kTcThreads, 2) map_tc_kernel(MapParams p, int 
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcRows)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(2 * kTcRows)
                  : "memory");
 }
 
 namespace {
 
-size_t tc_smem_bytes(int kk_max, size_t in_size) {
-  return (size_t)(kTcCols + kTcRows) * kk_max * 4 + (size_t)kTcRows * kTcCols * in_size;
+size_t tc_smem_bytes(int ks_max, size_t in_size) {
+  return (size_t)(kTcCols + 2 * kTcRows) * ks_max * 4 + 2 * (size_t)kTcRows * kTcCols * in_size;
 }
 
 template <typename TIn, typename TOut, bool VEC>
@@ -356,21 +414,26 @@ cudaError_t launch_tc_typed(const MapParams& p, int kk_max, cudaStream_t st) {
   const size_t smem = tc_smem_bytes(kk_max, sizeof(TIn));
   static int per_sm[4] = {-1, -1, -1, -1};  // by K' bucket
   static int sms = 0;
-  const int slot = kk_max / 24 - 1 > 3 ? 3 : kk_max / 24 - 1;
+  const int slot = kk_max / 16 - 1 > 3 ? 3 : kk_max / 16 - 1;
   if (per_sm[slot] < 0) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)tc_smem_bytes(kTcKMax, sizeof(TIn)));
+                         (int)tc_smem_bytes(kTcKsMax, sizeof(TIn)));
     cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kTcThreads, smem) != cudaSuccess) {
-      cudaGetLastError();
-      occ = 1;
-    }
-    // at most 8 CTAs x 64 TMEM columns fit one SM's 512 columns
-    per_sm[slot] = std::max(1, std::min(occ, 8));
+    // resident CTAs per SM from the kernel's own footprint (shared memory
+    // incl. the per-block reservation, registers), at most 4 for TMEM
+    int smem_sm = 0, reserved = 0, regs_sm = 0;
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    cudaFuncAttributes fa{};
+    cudaFuncGetAttributes(&fa, k);
+    const size_t per_cta = smem + fa.sharedSizeBytes + (size_t)reserved;
+    int fit = (int)((size_t)smem_sm / per_cta);
+    if (fa.numRegs > 0) fit = std::min(fit, regs_sm / (fa.numRegs * kTcThreads));
+    per_sm[slot] = std::max(1, std::min(fit, 4));
   }
   const int strips = (p.width + kTcCols - 1) / kTcCols;
   const long long items = (long long)p.n_frames * strips;
@@ -405,7 +468,7 @@ cudaError_t launch_map_tc(const MapParams& p, int window, int depth_dtype, int m
   if (p.n_frames <= 0) return cudaSuccess;
   if ((long long)p.n_frames * ((p.width + kTcCols - 1) / kTcCols) > 0x7fffffffLL)
     return cudaErrorInvalidConfiguration;
-  const int kk_max = 3 * ((std::min(std::max(window, 1), kMaxPts) + 7) & ~7);
+  const int kk_max = 2 * ((std::min(std::max(window, 1), kMaxPts) + 7) & ~7);  // stored K
   cudaError_t e;
   switch (depth_dtype) {
     case MF_F32: e = launch_tc_out<float>(p, map_dtype, kk_max, st); break;

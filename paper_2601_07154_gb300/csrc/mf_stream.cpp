@@ -229,6 +229,7 @@ struct mf_stream {
   double map_ms = 0.0;
   int64_t map_timed = 0;
   int64_t device_bytes = 0;
+  uint32_t last_map_kernel = 0;
 
   void* dalloc(size_t bytes) {
     void* p = nullptr;
@@ -812,6 +813,9 @@ int mf_get_maps(mf_stream* s, int32_t max_frames, void* focus_map, void* guided_
     }
     MF_CUDA(mf::launch_map(mp, s->d.window, s->d.depth_dtype, s->d.map_dtype, s->st, &s->launches),
             "map launch");
+    s->last_map_kernel = mf::map_uses_tensor_cores(mp.path, s->d.window, s->d.map_dtype)
+                             ? MF_FLAG_MAP_TENSOR_CORES
+                             : MF_FLAG_MAP_CUDA_CORES;
     if (timed) {
       MF_CUDA(cudaEventRecord(tp.b, s->st), "event record");
       s->timers.push_back(tp);
@@ -919,6 +923,8 @@ int mf_stream_stats(mf_stream* s, mf_stats* out) {
   out->map_launches = s->map_timed;
   out->map_kernel_ms = s->map_ms;
   out->device_bytes = s->device_bytes;
+  out->last_map_kernel = s->last_map_kernel;
+  out->reserved = 0;
   return MF_OK;
 }
 
