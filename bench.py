@@ -295,6 +295,7 @@ def run_gpu(args):
     if rank == 0:
         peak, kind = hbm_peak()
         achieved = frames * FRAME_BYTES / (map_ms / 1000.0) / 1e9
+        traffic = profiled_traffic(frames, map_kernel_name(s1))
         rec = {
             "metric": METRIC, "value": round(value, 2), "unit": "frames/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
@@ -306,7 +307,9 @@ def run_gpu(args):
             "roofline": {"bound": "hbm", "kernel": map_kernel_name(s1), "achieved": round(achieved, 1),
                          "peak": peak, "peak_kind": kind, "unit": "GB/s",
                          "frac": round(achieved / peak, 4),
-                         "traffic": profiled_traffic(frames, map_kernel_name(s1)),
+                         "traffic": traffic,
+                         "dram_frac": (round(traffic / (map_ms / 1000.0) / 1e9 / peak, 4)
+                                       if traffic else None),
                          "algorithmic_bytes_per_launch": frames * FRAME_BYTES,
                          "launch_ms": round(map_ms, 4)},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,

@@ -91,9 +91,9 @@ typedef enum { MF_NORM_COUNT = 0, MF_NORM_MAX = 1 } mf_norm;
  * column factor tables, so it can run on the CUDA cores (one FMA per point
  * and pixel) or on the tensor cores (tcgen05 with TMEM accumulators, three
  * TF32 products per FP32 term).  By default the library takes the faster
- * one as measured on GB300: the tensor cores for FP32 maps with windows up
- * to 16 points and for 16-bit maps with larger windows, the CUDA cores
- * otherwise.  These flags force one of them (not both). */
+ * one as measured on GB300: the tensor cores for 16-bit maps with windows
+ * above 16 points, the CUDA cores otherwise.  These flags force one of
+ * them (not both). */
 #define MF_FLAG_MAP_CUDA_CORES 8u
 #define MF_FLAG_MAP_TENSOR_CORES 16u
 

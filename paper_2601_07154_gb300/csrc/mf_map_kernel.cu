@@ -415,15 +415,15 @@ cudaError_t launch_n(const MapParams& p, int in_dtype, int out_dtype, cudaStream
 
 }  // namespace
 
-// The faster kernel as measured on 1080p streams (fraction of measured HBM
-// bandwidth, tensor vs CUDA cores): FP32 maps, windows 8 / 16: 1.10 / 1.03
-// vs 0.94 / 0.93; window 32: 0.67 vs 0.87 (the tensor-core kernel's
-// operands and depth buffers leave room for one CTA per SM).  16-bit maps,
-// windows 8 / 16: 0.61 / 0.56 vs 0.71 / 0.68; window 32: 0.52 vs 0.46.
+// The faster kernel as measured on 1080p x 304-frame ACCEL streams
+// (algorithmic bytes over time, as a fraction of measured HBM bandwidth;
+// both kernels skip the depth reads of units no point reaches), CUDA vs
+// tensor cores: FP32 maps, windows 8 / 16 / 32: 1.13 / 1.03 / 0.94 vs
+// 1.10 / 1.03 / 0.67; 16-bit maps: 0.83 / 0.72 / 0.48 vs 0.61 / 0.56 / 0.52.
 bool map_uses_tensor_cores(int path, int window, int map_dtype) {
   if (path == kMapTensorCores) return true;
   if (path == kMapCudaCores) return false;
-  return map_dtype == MF_F32 ? window <= 16 : window > 16;
+  return map_dtype != MF_F32 && window > 16;
 }
 
 cudaError_t launch_map(const MapParams& p, int window, int in_dtype, int out_dtype,

@@ -235,11 +235,7 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
       cp_async<kInBytes>(my_ring + (r & (S - 1)) * 32 + lane, dsrc + (size_t)r * dstride);
     cp_async_commit();
   };
-  // The first depth rows are requested before the set-up, so the copies are
-  // in flight while the factors are computed.  The ring is this warp's own
-  // and the previous unit drained it.
-#pragma unroll
-  for (int s = 0; s < S - 2; ++s) issue(s);
+  // The ring is this warp's own and the previous unit drained it.
   __syncthreads();  // the previous unit is done with P and Ey
 
   FrameRec* rec = ug.rec;
@@ -275,6 +271,12 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
   }
   __syncthreads();
   const int nk = s_kept;  // <= NMAX: n never exceeds the window's bucket
+  // Depth only scales G.  With no point kept the unit's M is 0 and so is
+  // G = M min(1, d0/D), whatever D holds: its depth rows are not read.
+  if (nk == 0 || !ug.G) dsrc = nullptr;
+  // the first depth rows are in flight while the factors are computed
+#pragma unroll
+  for (int s = 0; s < S - 2; ++s) issue(s);
   const int nc = min(NMAX, (nk + 3) & ~3);
   for (int r = warp; r < rows; r += kMapThreads / 32)
     for (int i = lane; i < nc; i += 32)
