@@ -87,6 +87,10 @@ struct MapParams {
   int path;                // kMapAuto, kMapCudaCores or kMapTensorCores
 };
 
+// MF_NORM_MAX applies to frames whose count-normalised map maximum is at
+// least this (smaller maxima: every point lies far outside the image).
+constexpr float kNormFloor = 0x1p-20f;
+
 // Map kernel selection (MapParams::path).
 constexpr int kMapAuto = 0;
 constexpr int kMapCudaCores = 1;
@@ -123,7 +127,9 @@ bool map_uses_tensor_cores(int path, int window, int map_dtype);
 // Tensor-core map kernel (mf_map_tc.cu); any width, any plane alignment.
 cudaError_t launch_map_tc(const MapParams& p, int window, int depth_dtype, int map_dtype,
                           cudaStream_t st, int64_t* launches);
-cudaError_t launch_map(const MapParams& p, int window, int in_dtype, int out_dtype,
+// launch_map renders the maps of p's frames with Z of Eq. 7 as `normalize`
+// (mf_norm) selects.
+cudaError_t launch_map(const MapParams& p, int window, int in_dtype, int out_dtype, int normalize,
                        cudaStream_t st, int64_t* launches);
 cudaError_t launch_finalize(const FinalizeParams& p, cudaStream_t st, int64_t* launches);
 cudaError_t launch_normalize(const NormalizeParams& p, int map_dtype, cudaStream_t st,

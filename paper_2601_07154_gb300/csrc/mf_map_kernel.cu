@@ -19,6 +19,7 @@
 // for c, so its relative error stays near one FP32 rounding; expf (full
 // precision) then costs at most 2 ulp per factor.
 #include <algorithm>
+#include <type_traits>
 
 #include "mf_map_unit.cuh"
 #include "mf_pose_device.cuh"
@@ -251,7 +252,7 @@ __global__ void __launch_bounds__(kMapThreads) map_kernel(MapParams p) {
 // Streaming kernel for frames whose rows allow CPT-pixel vector access (the
 // common case): persistent CTAs of 8 warps walk the frames' units (band of
 // up to 256 rows x group of 8 strips) in frame order; map_unit does the work.
-template <int NMAX, int CPT, typename TIn, typename TOut>
+template <int NMAX, int CPT, typename TIn, typename TOut, int MODE>
 __global__ void __launch_bounds__(kMapThreads, 2) map_stream_kernel(MapParams p, int band_h) {
   extern __shared__ float4 smem4[];
   float* Ey = reinterpret_cast<float*>(smem4);                          // [band_h][NMAX]
@@ -279,7 +280,7 @@ __global__ void __launch_bounds__(kMapThreads, 2) map_stream_kernel(MapParams p,
     ug.rows = min(band_h, p.height - ug.y0);
     ug.gx0 = g * kGroupW;
     ug.d0 = p.d0;
-    map_unit<NMAX, CPT, TIn, TOut>(ug, Ey, my_ring, P, s_kept);
+    map_unit<NMAX, CPT, TIn, TOut, MODE>(ug, Ey, my_ring, P, s_kept);
   }
 }
 
@@ -367,8 +368,36 @@ void occupancy(K k, size_t smem_max, int* per_sm, int* sms) {
   if (*per_sm < 1) *per_sm = 1;
 }
 
+template <typename T>
+constexpr int out_dtype_of() {
+  return std::is_same<T, float>::value ? MF_F32 : std::is_same<T, __half>::value ? MF_F16 : MF_BF16;
+}
+
+NormalizeParams normalize_params(const MapParams& p) {
+  NormalizeParams np{};
+  np.recs = p.recs;
+  np.rec_mask = p.rec_mask;
+  np.f0 = p.f0;
+  np.n_frames = p.n_frames;
+  np.plane = (int64_t)p.width * p.height;
+  np.M = p.M;
+  np.G = p.G;
+  return np;
+}
+
+// Launches the persistent kernel k over `units` units.
+template <typename K>
+void launch_persistent(K k, int* per_sm, int* sms, size_t smem_max, long long units, size_t smem,
+                       const MapParams& p, int band_h, cudaStream_t st) {
+  if (*per_sm < 0) occupancy(k, smem_max, per_sm, sms);
+  const long long grid = std::min<long long>(units, (long long)*sms * *per_sm);
+  k<<<(unsigned)grid, kMapThreads, smem, st>>>(p, band_h);
+}
+
+// One launch (or, for MF_NORM_MAX, a max-only pass then a scaled pass) of
+// the map kernel for NMAX-point windows; *nl receives the launch count.
 template <int NMAX, typename TIn, typename TOut>
-cudaError_t launch_typed(const MapParams& p, cudaStream_t st) {
+cudaError_t launch_typed(const MapParams& p, bool norm_max, cudaStream_t st, int64_t* nl) {
   const long long tiles = (long long)p.n_frames * p.tiles_x * p.tiles_y;
   if (tiles <= 0) return cudaSuccess;
   if (tiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
@@ -380,35 +409,51 @@ cudaError_t launch_typed(const MapParams& p, cudaStream_t st) {
   if (vec) {
     const int bands = (p.height + kBandMax - 1) / kBandMax;
     const int band_h = (p.height + bands - 1) / bands;
-    auto k = map_stream_kernel<NMAX, CPT, TIn, TOut>;
-    static int per_sm = -1, sms = 0;
-    if (per_sm < 0) occupancy(k, unit_smem_bytes(NMAX, kBandMax, CPT), &per_sm, &sms);
     constexpr int kGroupW = kGroupStrips * 32 * CPT;
     const long long units =
         (long long)p.n_frames * bands * ((p.width + kGroupW - 1) / kGroupW);
-    const long long grid = std::min<long long>(units, (long long)sms * per_sm);
-    k<<<(unsigned)grid, kMapThreads, unit_smem_bytes(NMAX, band_h, CPT), st>>>(p, band_h);
+    const size_t smem_max = unit_smem_bytes(NMAX, kBandMax, CPT), smem = unit_smem_bytes(NMAX, band_h, CPT);
+    static int per_sm[3] = {-1, -1, -1}, sms = 0;
+    if (!norm_max) {
+      launch_persistent(map_stream_kernel<NMAX, CPT, TIn, TOut, kUnitFull>, &per_sm[0], &sms,
+                        smem_max, units, smem, p, band_h, st);
+      *nl += 1;
+    } else {
+      // same units, same sums: the first pass only finds each frame's maximum
+      launch_persistent(map_stream_kernel<NMAX, CPT, float, float, kUnitMaxOnly>, &per_sm[1], &sms,
+                        smem_max, units, smem, p, band_h, st);
+      launch_persistent(map_stream_kernel<NMAX, CPT, TIn, TOut, kUnitScaled>, &per_sm[2], &sms,
+                        smem_max, units, smem, p, band_h, st);
+      *nl += 2;
+    }
   } else {
     const size_t smem = (size_t)NMAX * kTileW * 4 + (size_t)p.tile_h * NMAX * 4;
     auto k = map_kernel<NMAX, TIn, TOut, false>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k<<<(unsigned)tiles, kMapThreads, smem, st>>>(p);
+    *nl += 1;
+    if (norm_max) {
+      const cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+      return launch_normalize(normalize_params(p), out_dtype_of<TOut>(), st, nl);
+    }
   }
   return cudaGetLastError();
 }
 
 template <int NMAX>
-cudaError_t launch_n(const MapParams& p, int in_dtype, int out_dtype, cudaStream_t st) {
+cudaError_t launch_n(const MapParams& p, int in_dtype, int out_dtype, bool mx, cudaStream_t st,
+                     int64_t* nl) {
   switch (in_dtype * 3 + out_dtype) {
-    case MF_F32 * 3 + MF_F32: return launch_typed<NMAX, float, float>(p, st);
-    case MF_F32 * 3 + MF_BF16: return launch_typed<NMAX, float, __nv_bfloat16>(p, st);
-    case MF_F32 * 3 + MF_F16: return launch_typed<NMAX, float, __half>(p, st);
-    case MF_BF16 * 3 + MF_F32: return launch_typed<NMAX, __nv_bfloat16, float>(p, st);
-    case MF_BF16 * 3 + MF_BF16: return launch_typed<NMAX, __nv_bfloat16, __nv_bfloat16>(p, st);
-    case MF_BF16 * 3 + MF_F16: return launch_typed<NMAX, __nv_bfloat16, __half>(p, st);
-    case MF_F16 * 3 + MF_F32: return launch_typed<NMAX, __half, float>(p, st);
-    case MF_F16 * 3 + MF_BF16: return launch_typed<NMAX, __half, __nv_bfloat16>(p, st);
-    case MF_F16 * 3 + MF_F16: return launch_typed<NMAX, __half, __half>(p, st);
+    case MF_F32 * 3 + MF_F32: return launch_typed<NMAX, float, float>(p, mx, st, nl);
+    case MF_F32 * 3 + MF_BF16: return launch_typed<NMAX, float, __nv_bfloat16>(p, mx, st, nl);
+    case MF_F32 * 3 + MF_F16: return launch_typed<NMAX, float, __half>(p, mx, st, nl);
+    case MF_BF16 * 3 + MF_F32: return launch_typed<NMAX, __nv_bfloat16, float>(p, mx, st, nl);
+    case MF_BF16 * 3 + MF_BF16: return launch_typed<NMAX, __nv_bfloat16, __nv_bfloat16>(p, mx, st, nl);
+    case MF_BF16 * 3 + MF_F16: return launch_typed<NMAX, __nv_bfloat16, __half>(p, mx, st, nl);
+    case MF_F16 * 3 + MF_F32: return launch_typed<NMAX, __half, float>(p, mx, st, nl);
+    case MF_F16 * 3 + MF_BF16: return launch_typed<NMAX, __half, __nv_bfloat16>(p, mx, st, nl);
+    case MF_F16 * 3 + MF_F16: return launch_typed<NMAX, __half, __half>(p, mx, st, nl);
   }
   return cudaErrorInvalidValue;
 }
@@ -426,20 +471,18 @@ bool map_uses_tensor_cores(int path, int window, int map_dtype) {
   return map_dtype != MF_F32 && window > 16;
 }
 
-cudaError_t launch_map(const MapParams& p, int window, int in_dtype, int out_dtype,
+cudaError_t launch_map(const MapParams& p, int window, int in_dtype, int out_dtype, int normalize,
                        cudaStream_t st, int64_t* launches) {
   if (p.n_frames <= 0) return cudaSuccess;
-  if (map_uses_tensor_cores(p.path, window, out_dtype))
-    return launch_map_tc(p, window, in_dtype, out_dtype, st, launches);
-  cudaError_t e;
-  if (window <= 8)
-    e = launch_n<8>(p, in_dtype, out_dtype, st);
-  else if (window <= 16)
-    e = launch_n<16>(p, in_dtype, out_dtype, st);
-  else
-    e = launch_n<32>(p, in_dtype, out_dtype, st);
-  if (e == cudaSuccess) ++*launches;
-  return e;
+  const bool mx = normalize == MF_NORM_MAX;
+  if (map_uses_tensor_cores(p.path, window, out_dtype)) {
+    cudaError_t e = launch_map_tc(p, window, in_dtype, out_dtype, st, launches);
+    if (e == cudaSuccess && mx) e = launch_normalize(normalize_params(p), out_dtype, st, launches);
+    return e;
+  }
+  if (window <= 8) return launch_n<8>(p, in_dtype, out_dtype, mx, st, launches);
+  if (window <= 16) return launch_n<16>(p, in_dtype, out_dtype, mx, st, launches);
+  return launch_n<32>(p, in_dtype, out_dtype, mx, st, launches);
 }
 
 }  // namespace mf

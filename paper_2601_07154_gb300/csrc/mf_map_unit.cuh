@@ -214,7 +214,16 @@ struct UnitGeom {
   float d0;
 };
 
-template <int NMAX, int CPT, typename TIn, typename TOut>
+// What a pass over a unit produces.  Full: M, G and the frame's argmax.
+// MaxOnly: the argmax alone (no memory traffic), the first pass of
+// MF_NORM_MAX.  Scaled: M and G of the map divided by the frame's maximum
+// from that first pass -- the same FP32 sums, so the pixel holding the
+// maximum becomes exactly 1.
+constexpr int kUnitFull = 0;
+constexpr int kUnitMaxOnly = 1;
+constexpr int kUnitScaled = 2;
+
+template <int NMAX, int CPT, typename TIn, typename TOut, int MODE = kUnitFull>
 __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* my_ring,
                                          PointsSmem<kMaxPts>& P, int& s_kept) {
   constexpr int kInBytes = CPT * (int)sizeof(TIn);
@@ -227,7 +236,7 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
   const bool col_ok = xc < ug.width;
   const int gx1 = min(ug.width, ug.gx0 + kGroupStrips * kStrip) - 1;
   const size_t row0 = (size_t)y0 * ug.width + xc;
-  const char* dsrc = ug.depth ? ug.depth + row0 * sizeof(TIn) : nullptr;
+  const char* dsrc = (MODE != kUnitMaxOnly && ug.depth) ? ug.depth + row0 * sizeof(TIn) : nullptr;
   const size_t dstride = (size_t)ug.width * sizeof(TIn);
   static_assert((S & (S - 1)) == 0, "ring stages must be a power of two");
   auto issue = [&](int r) {
@@ -304,8 +313,18 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
   float best = -1.0f;
   unsigned bidx = 0;
   // output rows advance by a stride: no per-row 64-bit multiply
-  char* mrow = ug.M ? ug.M + row0 * sizeof(TOut) : nullptr;
-  char* grow = ug.G ? ug.G + row0 * sizeof(TOut) : nullptr;
+  char* mrow = (MODE != kUnitMaxOnly && ug.M) ? ug.M + row0 * sizeof(TOut) : nullptr;
+  char* grow = (MODE != kUnitMaxOnly && ug.G) ? ug.G + row0 * sizeof(TOut) : nullptr;
+  // Scaled pass: divide by the maximum the first pass found (IEEE reciprocal
+  // once per unit, then a product; the maximum itself maps to exactly 1)
+  float mx = 0.0f, inv = 1.0f;
+  bool scale = false;
+  if (MODE == kUnitScaled) {
+    const unsigned long long key = rec->argmax_key;
+    mx = __uint_as_float((unsigned)(key >> 32));
+    scale = n > 0 && key != 0ull && mx >= kNormFloor;
+    inv = scale ? 1.0f / mx : 1.0f;
+  }
   const size_t ostride = (size_t)ug.width * sizeof(TOut);
   auto emit = [&](const float2 (&acc)[CPT / 2], const float (&dv)[CPT], int r, size_t off) {
     float m[CPT];
@@ -313,6 +332,10 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
     for (int c = 0; c < CPT / 2; ++c) {
       m[2 * c] = acc[c].x;
       m[2 * c + 1] = acc[c].y;
+    }
+    if (MODE == kUnitScaled && scale) {
+#pragma unroll
+      for (int c = 0; c < CPT; ++c) m[c] = m[c] == mx ? 1.0f : m[c] * inv;
     }
     if (mrow) Vec<TOut, CPT>::store(mrow + off, 0, m);
     if (grow) {
@@ -374,9 +397,11 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
     else
       accum_two_rows<NMAX, CPT, 0>(ex, ey0, ey1, nc, a, b);
     if (!col_ok) continue;
-    emit(a, d0v, r, off);
-    if (two) emit(b, d1v, r + 1, off + ostride);
-    track(a, b, two, r);
+    if (MODE != kUnitMaxOnly) {
+      emit(a, d0v, r, off);
+      if (two) emit(b, d1v, r + 1, off + ostride);
+    }
+    if (MODE != kUnitScaled) track(a, b, two, r);
   }
   cp_async_wait<0>();
   unsigned long long key =
@@ -385,7 +410,7 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
     const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
     key = k2 > key ? k2 : key;
   }
-  if (lane == 0 && n > 0 && key) atomicMax(&rec->argmax_key, key);
+  if (MODE != kUnitScaled && lane == 0 && n > 0 && key) atomicMax(&rec->argmax_key, key);
 }
 
 // Dynamic shared memory of a CTA running units of bucket NMAX with CPT

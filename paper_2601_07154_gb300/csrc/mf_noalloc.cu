@@ -157,18 +157,7 @@ extern "C" int mf_render_noalloc(const mf_stream_desc* d, int32_t n_poses,
     mp.G = guided_depth;
     mp.d0 = (float)d->depth_ref_m;
     mp.path = mf::host_map_path(d->flags);
-    e = mf::launch_map(mp, d->window, d->depth_dtype, d->map_dtype, st, &launches);
-  }
-  if (e == cudaSuccess && d->normalize == MF_NORM_MAX) {
-    mf::NormalizeParams np{};
-    np.recs = recs;
-    np.rec_mask = kRecSlots - 1;
-    np.f0 = e0;
-    np.n_frames = n_render;
-    np.plane = (int64_t)d->width * d->height;
-    np.M = focus_map;
-    np.G = guided_depth;
-    e = mf::launch_normalize(np, d->map_dtype, st, &launches);
+    e = mf::launch_map(mp, d->window, d->depth_dtype, d->map_dtype, d->normalize, st, &launches);
   }
   if (e == cudaSuccess && info) {
     mf::FinalizeParams fp{};

@@ -273,7 +273,6 @@ __device__ __forceinline__ void frame_points(const double* ring, const int32_t* 
 // points all lie far outside the image keeps its near-zero count-normalised
 // maps).  Dividing, rather than multiplying by a reciprocal, maps the
 // maximum to exactly 1.
-constexpr float kNormFloor = 0x1p-20f;
 __device__ __forceinline__ float norm_divisor(const FrameRec* rec) {
   const unsigned long long key = rec->argmax_key;
   if (rec->n_valid <= 0 || key == 0ull) return 1.0f;

@@ -811,7 +811,8 @@ int mf_get_maps(mf_stream* s, int32_t max_frames, void* focus_map, void* guided_
       if (rc) return rc;
       MF_CUDA(cudaEventRecord(tp.a, s->st), "event record");
     }
-    MF_CUDA(mf::launch_map(mp, s->d.window, s->d.depth_dtype, s->d.map_dtype, s->st, &s->launches),
+    MF_CUDA(mf::launch_map(mp, s->d.window, s->d.depth_dtype, s->d.map_dtype, s->d.normalize, s->st,
+                           &s->launches),
             "map launch");
     s->last_map_kernel = mf::map_uses_tensor_cores(mp.path, s->d.window, s->d.map_dtype)
                              ? MF_FLAG_MAP_TENSOR_CORES
@@ -819,17 +820,6 @@ int mf_get_maps(mf_stream* s, int32_t max_frames, void* focus_map, void* guided_
     if (timed) {
       MF_CUDA(cudaEventRecord(tp.b, s->st), "event record");
       s->timers.push_back(tp);
-    }
-    if (s->d.normalize == MF_NORM_MAX) {
-      mf::NormalizeParams np{};
-      np.recs = s->recs;
-      np.rec_mask = s->rec_cap - 1;
-      np.f0 = f;
-      np.n_frames = cnt;
-      np.plane = (int64_t)s->d.width * s->d.height;
-      np.M = Mp;
-      np.G = Gp;
-      MF_CUDA(mf::launch_normalize(np, s->d.map_dtype, s->st, &s->launches), "normalize launch");
     }
     if (maps_host) {
       if (pending.slot >= 0) {

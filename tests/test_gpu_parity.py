@@ -190,14 +190,18 @@ def test_calibration_rescale(mf):
     compare_all(M, G, info, pts, ref, K)
 
 
-@pytest.mark.parametrize("mode,storage", [("accel", "f32"), ("heading", "f32"),
-                                          ("heading", "bf16"), ("accel", "f16")])
-def test_max_normalised_maps(mf, mode, storage):
-    """Z = the map maximum: each frame's maps divided by its FP32 maximum."""
+@pytest.mark.parametrize("mode,storage,kernel", [
+    ("accel", "f32", "cuda_cores"), ("heading", "f32", "cuda_cores"),
+    ("heading", "bf16", "cuda_cores"), ("accel", "f16", "cuda_cores"),
+    ("heading", "f32", "tensor_cores"), ("accel", "bf16", "tensor_cores")])
+def test_max_normalised_maps(mf, mode, storage, kernel):
+    """Z = the map maximum: each frame's maps divided by its FP32 maximum
+    (CUDA cores: a max-only pass, then a pass that renders the scaled map;
+    tensor cores: the map, then an in-place division)."""
     w = small_stream()
     M, G, info, pts, ref = run_both(mf, w.poses, w.depth_stack(0, 64), w.K(), 320, 240,
                                     window=8, smooth_len=15, mode=mode, storage=storage,
-                                    normalize="max")
+                                    normalize="max", map_kernel=kernel)
     assert len(info) == ref.n_emitted
     cref = O.Params(320, 240, window=8, smooth_len=15, mode=_mode(mode))
     cst = O.OracleStream(cref)
