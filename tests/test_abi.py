@@ -51,6 +51,8 @@ def test_static_queries(mf):
     dict(width=10, height=10, overlap=2), dict(width=10, height=10, pose_frame=1, overlap=0),
     dict(width=10, height=10, depth_dtype=7), dict(width=10, height=10, sigma_rel=0.0),
     dict(width=10, height=10, s_lo=2.0, s_hi=1.0), dict(width=20000, height=10),
+    dict(width=10, height=10, normalize=2), dict(width=10, height=10, normalize=-1),
+    dict(width=10, height=10, flags=8 | 16),
 ])
 def test_invalid_descriptors_rejected_before_any_device_work(mf, fields):
     d = mf.mf_stream_desc_init(**fields)
@@ -63,3 +65,14 @@ def test_null_arguments(mf):
     assert mf._mf.lib.mf_push_frames(None, 1, None, None, None) == mf.MF_ERR_INVALID_ARG
     assert mf._mf.lib.mf_get_maps(None, 1, None, None, None, None, None, 0) == mf.MF_ERR_INVALID_ARG
     assert mf._mf.lib.mf_close_stream(None) == mf.MF_OK
+
+
+def test_struct_layouts_match_the_header(mf):
+    """ctypes mirrors of the C structs: sizes that the header fixes."""
+    import ctypes
+    assert ctypes.sizeof(mf._mf.MFStats) == 7 * 8 + 2 * 4
+    assert mf._mf.FRAME_INFO_DTYPE.itemsize == 64
+    assert mf._mf.MOTION_POINT_DTYPE.itemsize == 40
+    assert mf._mf.PUSH_DTYPE.itemsize == 64
+    assert mf._mf.MF_FLAG_MAP_CUDA_CORES & mf._mf.MF_FLAG_MAP_TENSOR_CORES == 0
+    assert (mf._mf.MF_FLAG_MAP_CUDA_CORES | mf._mf.MF_FLAG_MAP_TENSOR_CORES) & mf._mf.MF_FLAG_TIME_KERNELS == 0
