@@ -182,11 +182,13 @@ def test_ragged_and_tiny_frames(mf, width, height, kernel):
     compare_all(M, G, info, pts, ref, K)
 
 
-def test_calibration_rescale(mf):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_calibration_rescale(mf, kernel):
+    """Intrinsics at twice the map resolution; no depth pushed (G = 0)."""
     poses = _accelerating_walk(40)
     K = np.array([520.0, 520.0, 319.5, 239.5])
     M, G, info, pts, ref = run_both(mf, poses, None, K, 320, 240, window=8, smooth_len=5,
-                                    mode="heading", calib=(640, 480))
+                                    mode="heading", calib=(640, 480), map_kernel=kernel)
     compare_all(M, G, info, pts, ref, K)
 
 
@@ -251,7 +253,8 @@ def test_degenerate_constant_velocity_is_empty(mf):
     assert np.all(info["argmax_x"] == -1)
 
 
-def test_bad_pose_and_invalid_depth(mf):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_bad_pose_and_invalid_depth(mf, kernel):
     poses = _accelerating_walk(30)
     poses[12, 0, 0] = 1.01
     depth = np.full((30, 48, 64), 2.0, np.float32)
@@ -261,7 +264,8 @@ def test_bad_pose_and_invalid_depth(mf):
     depth[:, 3, :] = -1.0
     depth[:, 4, :] = 0.5
     K = np.array([50.0, 50.0, 32.0, 24.0])
-    M, G, info, pts, ref = run_both(mf, poses, depth, K, 64, 48, window=4, smooth_len=3)
+    M, G, info, pts, ref = run_both(mf, poses, depth, K, 64, 48, window=4, smooth_len=3,
+                                    map_kernel=kernel)
     compare_all(M, G, info, pts, ref, K)
     assert info["status"][12] == O.FRAME_BAD_POSE and info["valid_mask"][13] == 0b0011
     assert not G[:, :4].any() and np.array_equal(G[:, 4], M[:, 4])
