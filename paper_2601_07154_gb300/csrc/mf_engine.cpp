@@ -108,8 +108,16 @@ struct Slot {
   int64_t pending_tick = -1;  // tick id of the slot's queued push
   int64_t last_tick = -1;     // last tick that used the slot
   size_t plane_in = 0, plane_out = 0;
+  int path = 0;                        // map path (mf::kEnginePaths)
   int band_h = 0, bands = 0, groups_x = 0;
 };
+
+// Columns per map unit of a path.
+int path_group_w(int path) { return path ? mf::kEngineWideGroupW : mf::kEngineGroupW; }
+
+// The 16-point, 4-columns-per-lane path serves windows up to 16 points on
+// widths divisible by 4; every other stream takes the 32-point path.
+int stream_path(int width, int window) { return window <= mf::kEngineWideNMAX && width % 4 == 0 ? 1 : 0; }
 
 }  // namespace
 
@@ -117,6 +125,7 @@ struct mf_engine {
   mf_engine_desc d{};
   int device = 0;
   cudaStream_t st = nullptr, cap_st = nullptr;
+  mf::EngineFork fork{};  // side stream and events of the concurrent map paths
   bool own_stream = false;
   std::vector<Slot> slots;
   SlotParams* slots_dev = nullptr;  // max_streams + 1 entries (the last: tuner)
@@ -134,7 +143,7 @@ struct mf_engine {
   cudaEvent_t done[2] = {nullptr, nullptr};
   cudaEvent_t t0[2] = {nullptr, nullptr};
   int64_t buf_tick[2] = {-1, -1};
-  int map_grid = 0;
+  mf::EngineGrids grids{};
   // the tick being assembled
   std::vector<TickPush> pushes;
   std::vector<TickFrame> frames;
@@ -181,36 +190,48 @@ namespace {
 size_t table_bytes(size_t frames, size_t pushes, size_t poses) {
   size_t off = align256(sizeof(TickHeader));
   off = align256(off + frames * sizeof(TickFrame));
+  off = align256(off + frames * sizeof(int32_t));
   off = align256(off + pushes * sizeof(TickPush));
   return off + poses * 12 * sizeof(double);
 }
 
-// Writes the tick being assembled (or a given frame list) into table `tab`;
-// returns the bytes used.
-size_t write_table(char* tab, const std::vector<TickFrame>& frames, const std::vector<TickPush>& pushes,
-                   const std::vector<double>& poses, int64_t n_units) {
+// Numbers every frame's units within its map path and writes the tick (or a
+// given frame list) into table `tab`; returns the bytes used.
+size_t write_table(char* tab, std::vector<TickFrame>& frames, const std::vector<TickPush>& pushes,
+                   const std::vector<double>& poses, int64_t* units_out) {
   TickHeader h{};
+  std::vector<int32_t> order;
+  order.reserve(frames.size());
+  for (int p = 0; p < mf::kEnginePaths; ++p) {
+    int64_t u = 0;
+    int32_t nf = 0;
+    for (size_t t = 0; t < frames.size(); ++t) {
+      TickFrame& f = frames[t];
+      if (f.path != p) continue;
+      f.unit_begin = u;
+      u += (int64_t)f.bands * f.groups_x;
+      order.push_back((int32_t)t);
+      ++nf;
+    }
+    h.n_units_path[p] = u;
+    h.n_frames_path[p] = nf;
+    h.n_units += u;
+  }
   h.n_frames = (int32_t)frames.size();
   h.n_pushes = (int32_t)pushes.size();
-  h.n_units = n_units;
   h.frames_off = (int64_t)align256(sizeof(TickHeader));
-  h.pushes_off = (int64_t)align256(h.frames_off + frames.size() * sizeof(TickFrame));
+  h.order_off = (int64_t)align256(h.frames_off + frames.size() * sizeof(TickFrame));
+  h.pushes_off = (int64_t)align256(h.order_off + frames.size() * sizeof(int32_t));
   h.poses_off = (int64_t)align256(h.pushes_off + pushes.size() * sizeof(TickPush));
   std::memcpy(tab, &h, sizeof(h));
-  if (!frames.empty()) std::memcpy(tab + h.frames_off, frames.data(), frames.size() * sizeof(TickFrame));
+  if (!frames.empty()) {
+    std::memcpy(tab + h.frames_off, frames.data(), frames.size() * sizeof(TickFrame));
+    std::memcpy(tab + h.order_off, order.data(), order.size() * sizeof(int32_t));
+  }
   if (!pushes.empty()) std::memcpy(tab + h.pushes_off, pushes.data(), pushes.size() * sizeof(TickPush));
   if (!poses.empty()) std::memcpy(tab + h.poses_off, poses.data(), poses.size() * sizeof(double));
+  if (units_out) *units_out = h.n_units;
   return (size_t)h.poses_off + poses.size() * sizeof(double);
-}
-
-// Assigns unit_begin to every frame; returns the unit count.
-int64_t number_units(std::vector<TickFrame>& frames) {
-  int64_t u = 0;
-  for (TickFrame& f : frames) {
-    f.unit_begin = u;
-    u += (int64_t)f.bands * f.groups_x;
-  }
-  return u;
 }
 
 mf::EngineKernelArgs kernel_args(mf_engine* e, int b) {
@@ -229,7 +250,7 @@ int build_graphs(mf_engine* e) {
                                      cudaMemcpyHostToDevice, e->cap_st);
     int64_t dummy = 0;
     cudaError_t c2 = mf::launch_engine_tick(kernel_args(e, b), e->d.depth_dtype, e->d.map_dtype,
-                                            e->map_grid, e->cap_st, &dummy);
+                                            e->grids, e->cap_st, e->fork, &dummy);
     cudaGraph_t g = nullptr;
     cudaError_t c3 = cudaStreamEndCapture(e->cap_st, &g);
     if (c1 != cudaSuccess || c2 != cudaSuccess || c3 != cudaSuccess)
@@ -270,6 +291,12 @@ void destroy(mf_engine* e) {
   e->dfree(e->recs, (size_t)e->d.max_tick_frames * sizeof(FrameRec));
   e->dfree(e->slots_dev, (size_t)(e->d.max_streams + 1) * sizeof(SlotParams));
   if (e->cap_st) cudaStreamDestroy(e->cap_st);
+  if (e->fork.side) {
+    cudaStreamSynchronize(e->fork.side);
+    cudaStreamDestroy(e->fork.side);
+  }
+  if (e->fork.fork) cudaEventDestroy(e->fork.fork);
+  if (e->fork.join) cudaEventDestroy(e->fork.join);
   if (e->own_stream && e->st) cudaStreamDestroy(e->st);
   delete e;
 }
@@ -404,6 +431,7 @@ int tune_class(mf_engine* e, int width, int height, int window, int* band_out) {
   std::vector<TickPush> pushes(1);
   pushes[0].slot = e->d.max_streams;
   std::vector<double> no_poses;
+  const int path = stream_path(width, window);
   for (int bh : band_candidates(height)) {
     std::vector<TickFrame> frs(frames);
     for (int f = 0; f < frames; ++f) {
@@ -412,28 +440,28 @@ int tune_class(mf_engine* e, int width, int height, int window, int* band_out) {
       t.push = 0;
       t.k = f;
       t.bucket = window;
+      t.path = path;
       t.band_h = bh;
       t.bands = (height + bh - 1) / bh;
-      t.groups_x = (width + mf::kEngineGroupW - 1) / mf::kEngineGroupW;
+      t.groups_x = (width + path_group_w(path) - 1) / path_group_w(path);
       char* base = buf + (size_t)f * per_frame;
       t.depth = base;
       t.M = base + pin * dtype_bytes(e->d.depth_dtype);
       t.G = t.M + pin * dtype_bytes(e->d.map_dtype);
       t.info = nullptr;
     }
-    const int64_t units = number_units(frs);
-    const size_t used = write_table(e->host_tab[0], frs, pushes, no_poses, units);
+    const size_t used = write_table(e->host_tab[0], frs, pushes, no_poses, nullptr);
     ENG_CUDA(cudaMemcpyAsync(e->dev_tab[0], e->host_tab[0], used, cudaMemcpyHostToDevice, e->st), "table");
     const mf::EngineKernelArgs args = kernel_args(e, 0);
-    ENG_CUDA(mf::launch_engine_map_only(args, e->d.depth_dtype, e->d.map_dtype, e->map_grid, e->st), "tune");
+    ENG_CUDA(mf::launch_engine_map_only(args, e->d.depth_dtype, e->d.map_dtype, e->grids, e->st), "tune");
     ENG_CUDA(cudaEventRecord(a, e->st), "event");
     for (int rep = 0; rep < 3; ++rep)
-      ENG_CUDA(mf::launch_engine_map_only(args, e->d.depth_dtype, e->d.map_dtype, e->map_grid, e->st), "tune");
+      ENG_CUDA(mf::launch_engine_map_only(args, e->d.depth_dtype, e->d.map_dtype, e->grids, e->st), "tune");
     ENG_CUDA(cudaEventRecord(b2, e->st), "event");
     ENG_CUDA(cudaEventSynchronize(b2), "event");
     float ms = 0.0f;
     ENG_CUDA(cudaEventElapsedTime(&ms, a, b2), "elapsed");
-    e->launches += 4;
+    e->launches += 4 * mf::kEnginePaths;
     if (ms < best_ms) {
       best_ms = ms;
       best_band = bh;
@@ -502,9 +530,12 @@ int mf_engine_open(const mf_engine_desc* d, mf_engine** out) {
     }
     e->own_stream = true;
   }
-  if (cudaStreamCreateWithFlags(&e->cap_st, cudaStreamNonBlocking) != cudaSuccess) {
+  if (cudaStreamCreateWithFlags(&e->cap_st, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&e->fork.side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&e->fork.fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&e->fork.join, cudaEventDisableTiming) != cudaSuccess) {
     destroy(e);
-    return fail(MF_ERR_CUDA, "capture stream creation");
+    return fail(MF_ERR_CUDA, "stream or event creation");
   }
   e->slots_dev = (SlotParams*)e->dalloc((size_t)(d->max_streams + 1) * sizeof(SlotParams));
   // every slot's pose history is allocated now, so admission never allocates
@@ -535,13 +566,13 @@ int mf_engine_open(const mf_engine_desc* d, mf_engine** out) {
     destroy(e);
     return fail(MF_ERR_ADMISSION, "engine tables exceed the memory budget");
   }
-  e->map_grid = mf::engine_map_grid(d->depth_dtype, d->map_dtype);
+  e->grids = mf::engine_map_grids(d->depth_dtype, d->map_dtype);
   // an empty table in both buffers, so a graph replay with nothing to do is harmless
   for (int b = 0; b < 2; ++b) {
     std::vector<TickFrame> nf;
     std::vector<TickPush> np;
     std::vector<double> npo;
-    const size_t used = write_table(e->host_tab[b], nf, np, npo, 0);
+    const size_t used = write_table(e->host_tab[b], nf, np, npo, nullptr);
     if (cudaMemcpy(e->dev_tab[b], e->host_tab[b], used, cudaMemcpyHostToDevice) != cudaSuccess) {
       destroy(e);
       return fail(MF_ERR_CUDA, "table init");
@@ -598,9 +629,10 @@ int mf_engine_add_stream(mf_engine* e, const mf_stream_desc* d, int64_t reserve_
   s.reserve = reserve_bytes;
   s.plane_in = (size_t)d->width * d->height * dtype_bytes(d->depth_dtype);
   s.plane_out = (size_t)d->width * d->height * dtype_bytes(d->map_dtype);
+  s.path = stream_path(d->width, std::min(d->window, (int)mf::kMaxPts));
   s.band_h = band;
   s.bands = (d->height + band - 1) / band;
-  s.groups_x = (d->width + mf::kEngineGroupW - 1) / mf::kEngineGroupW;
+  s.groups_x = (d->width + path_group_w(s.path) - 1) / path_group_w(s.path);
   // stream-ordered upload from pinned staging: earlier ticks never read this
   // slot (it was free), later ticks see it; nothing waits
   fill_slot_params(s, w, e->slots_pinned + free_slot);
@@ -661,6 +693,18 @@ int mf::engine_submit_at(mf_engine* e, int32_t slot, int32_t n, const double* po
       (guided_depth && (uintptr_t)guided_depth % (2 * dtype_bytes(e->d.map_dtype))) ||
       (info && (uintptr_t)info % 8))
     return fail(MF_ERR_INVALID_ARG, "misaligned plane or record pointer");
+  // the wide path reads and writes four elements at a time; a push whose
+  // planes are not aligned to that runs on the 32-point path
+  int path = s.path, band_h = s.band_h, bands = s.bands, groups_x = s.groups_x;
+  if (path == 1 &&
+      ((depth && (uintptr_t)depth % (4 * dtype_bytes(e->d.depth_dtype))) ||
+       (focus_map && (uintptr_t)focus_map % (4 * dtype_bytes(e->d.map_dtype))) ||
+       (guided_depth && (uintptr_t)guided_depth % (4 * dtype_bytes(e->d.map_dtype))))) {
+    path = 0;
+    band_h = default_band(s.d.height);
+    bands = (s.d.height + band_h - 1) / band_h;
+    groups_x = (s.d.width + path_group_w(0) - 1) / path_group_w(0);
+  }
   TickPush ps{};
   ps.slot = slot;
   ps.n = n;
@@ -677,9 +721,10 @@ int mf::engine_submit_at(mf_engine* e, int32_t slot, int32_t n, const double* po
     t.push = push_idx;
     t.k = k;
     t.bucket = s.d.window;
-    t.band_h = s.band_h;
-    t.bands = s.bands;
-    t.groups_x = s.groups_x;
+    t.path = path;
+    t.band_h = band_h;
+    t.bands = bands;
+    t.groups_x = groups_x;
     t.depth = depth ? static_cast<const char*>(depth) + (size_t)(O + k) * s.plane_in : nullptr;
     t.M = focus_map ? static_cast<char*>(focus_map) + (size_t)k * s.plane_out : nullptr;
     t.G = guided_depth ? static_cast<char*>(guided_depth) + (size_t)k * s.plane_out : nullptr;
@@ -723,8 +768,8 @@ int mf_engine_tick(mf_engine* e, int64_t* tick) {
     const int rc = wait_event(e->done[b], -1);
     if (rc) return rc;
   }
-  const int64_t units = number_units(e->frames);
-  const size_t used = write_table(e->host_tab[b], e->frames, e->pushes, e->poses, units);
+  int64_t units = 0;
+  const size_t used = write_table(e->host_tab[b], e->frames, e->pushes, e->poses, &units);
   cudaEvent_t ta = nullptr, tb = nullptr;
   if (e->d.flags & MF_FLAG_TIME_KERNELS) {
     ENG_CUDA(cudaEventCreate(&ta), "event");
@@ -737,14 +782,14 @@ int mf_engine_tick(mf_engine* e, int64_t* tick) {
              "graph copy update");
     ENG_CUDA(cudaGraphLaunch(e->exec[b], e->st), "graph launch");
     ++e->graph_launches;
-    e->launches += 4;
+    e->launches += mf::kEngineTickLaunches;
   } else {
     ENG_CUDA(cudaMemcpyAsync(e->dev_tab[b], e->host_tab[b], used, cudaMemcpyHostToDevice, e->st), "table");
-    ENG_CUDA(mf::launch_engine_tick(kernel_args(e, b), e->d.depth_dtype, e->d.map_dtype, e->map_grid,
-                                    e->st, &e->launches),
+    ENG_CUDA(mf::launch_engine_tick(kernel_args(e, b), e->d.depth_dtype, e->d.map_dtype, e->grids,
+                                    e->st, e->fork, &e->launches),
              "tick launch");
   }
-  mf::host_count_launches(4);
+  mf::host_count_launches(mf::kEngineTickLaunches);
   if (ta) {
     ENG_CUDA(cudaEventRecord(tb, e->st), "event");
     e->pending_timers.emplace_back(ta, tb);

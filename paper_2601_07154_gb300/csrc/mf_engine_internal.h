@@ -7,8 +7,15 @@
 
 namespace mf {
 
-constexpr int kEngineCPT = 2;                           // columns per lane in the batched map
+// Two map paths: every stream can take the 32-point path with 2 columns per
+// lane; streams with windows up to 16 points and widths divisible by 4 take
+// the 16-point path with 4 columns per lane (fewer instructions per pixel).
+constexpr int kEngineCPT = 2;                           // columns per lane, 32-point path
 constexpr int kEngineGroupW = 8 * 32 * kEngineCPT;      // columns per map unit
+constexpr int kEngineWideNMAX = 16;
+constexpr int kEngineWideCPT = 4;
+constexpr int kEngineWideGroupW = 8 * 32 * kEngineWideCPT;
+constexpr int kEnginePaths = 2;                         // 0: 32-point, 1: 16-point wide
 
 // Per admitted stream, written once at admission (device array by slot).
 struct SlotParams {
@@ -37,6 +44,8 @@ struct TickFrame {
   int32_t push;            // index into the tick's pushes
   int32_t k;               // emitted offset within the push
   int32_t bucket;          // window of the stream (informational)
+  int32_t path;            // map path (0: 32-point, 1: 16-point wide)
+  int32_t pad;
   int32_t band_h;          // tile height (autotuned per resolution class)
   int32_t groups_x;        // strip groups across the frame
   int32_t bands;
@@ -47,12 +56,20 @@ struct TickFrame {
   mf_frame_info* info;     // record (device) or NULL
 };
 
-// Layout of one tick table (header, frames, pushes, poses; each 256-B aligned).
+// Layout of one tick table (header, frames, path order, pushes, poses; each
+// 256-B aligned).  The path order lists the frame indices of path 0, then
+// those of path 1; unit_begin counts within the frame's path.
 struct TickHeader {
   int32_t n_frames, n_pushes;
-  int64_t n_units;
-  int64_t frames_off, pushes_off, poses_off;  // byte offsets from the header
-  int64_t pad[3];
+  int64_t n_units;                             // both paths
+  int64_t frames_off, order_off, pushes_off, poses_off;  // byte offsets from the header
+  int64_t n_units_path[kEnginePaths];
+  int32_t n_frames_path[kEnginePaths];
+};
+
+// Persistent grid of each path's map kernel.
+struct EngineGrids {
+  int g[kEnginePaths];
 };
 
 struct EngineKernelArgs {
@@ -62,14 +79,22 @@ struct EngineKernelArgs {
   int max_frames;              // capacity (grid sizes of the per-frame kernels)
 };
 
+// Kernel launches of one tick: ingest, points, the two map paths, finalize.
+// The two map paths run concurrently: the 16-point path on `side`, forked
+// from and joined back into `st` through the two events.
+constexpr int kEngineTickLaunches = 5;
+struct EngineFork {
+  cudaStream_t side;
+  cudaEvent_t fork, join;
+};
 cudaError_t launch_engine_tick(const EngineKernelArgs& a, int depth_dtype, int map_dtype,
-                               int map_grid, cudaStream_t st, int64_t* launches);
-// Resident CTAs per SM x SMs for the batched map kernel of a dtype pair.
-int engine_map_grid(int depth_dtype, int map_dtype);
-size_t engine_map_smem();
-// Times the batched map kernel over the given table (already on the device).
+                               const EngineGrids& grids, cudaStream_t st, const EngineFork& fk,
+                               int64_t* launches);
+// Resident CTAs per SM x SMs for each path's batched map kernel of a dtype pair.
+EngineGrids engine_map_grids(int depth_dtype, int map_dtype);
+// Runs both map paths over the given table (already on the device).
 cudaError_t launch_engine_map_only(const EngineKernelArgs& a, int depth_dtype, int map_dtype,
-                                   int map_grid, cudaStream_t st);
+                                   const EngineGrids& grids, cudaStream_t st);
 
 // mf_engine_submit with an explicit submit time (steady-clock ns) for the
 // latency statistics; the serving loop passes its clients' submit times.

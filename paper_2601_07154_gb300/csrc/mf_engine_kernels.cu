@@ -15,6 +15,9 @@ namespace {
 __device__ __forceinline__ const TickFrame* tick_frames(const TickHeader* t) {
   return reinterpret_cast<const TickFrame*>(reinterpret_cast<const char*>(t) + t->frames_off);
 }
+__device__ __forceinline__ const int32_t* tick_order(const TickHeader* t) {
+  return reinterpret_cast<const int32_t*>(reinterpret_cast<const char*>(t) + t->order_off);
+}
 __device__ __forceinline__ const TickPush* tick_pushes(const TickHeader* t) {
   return reinterpret_cast<const TickPush*>(reinterpret_cast<const char*>(t) + t->pushes_off);
 }
@@ -48,38 +51,41 @@ __global__ void __launch_bounds__(kEngPtsWarps * 32) engine_points_kernel(Engine
   frame_points(sp.ring, sp.ring_bad, sp.ring_mask, ps.e0 + fr.k, sp.fp, ps.K, sp.w, a.recs + t, S[wi]);
 }
 
-// Eq. 7 + guided depth: persistent CTAs over every frame's units.  One path
-// serves every window (up to 32 points, 2 columns per lane): a kernel holding
-// the 8/16-point paths as well would not fit the register budget.
-template <typename TIn, typename TOut>
+// Eq. 7 + guided depth: persistent CTAs over the units of one map path's
+// frames.  Each path is its own kernel: one kernel holding both the 16- and
+// the 32-point unit would not fit the register budget.
+template <typename TIn, typename TOut, int NMAX, int CPT, int PATH>
 __global__ void __launch_bounds__(kMapThreads, 2) engine_map_kernel(EngineKernelArgs a) {
   extern __shared__ float4 smem4[];
   __shared__ PointsSmem<kMaxPts> P;
   __shared__ int s_kept;
+  constexpr int kGroupW = 8 * 32 * CPT;
   const TickHeader* tab = a.table;
-  const int nf = tab->n_frames;
-  const long long units = tab->n_units;
+  const int nf = tab->n_frames_path[PATH];
+  const long long units = tab->n_units_path[PATH];
   const TickFrame* frames = tick_frames(tab);
+  const int32_t* order = tick_order(tab) + (PATH ? tab->n_frames_path[0] : 0);
   const TickPush* pushes = tick_pushes(tab);
   float* Ey = reinterpret_cast<float*>(smem4);
-  uint4* ring = reinterpret_cast<uint4*>(Ey + (size_t)kBandMax * kMaxPts);
-  uint4* my_ring = ring + (size_t)(threadIdx.x >> 5) * ring_stages(kEngineCPT) * 32;
+  uint4* ring = reinterpret_cast<uint4*>(Ey + (size_t)kBandMax * NMAX);
+  uint4* my_ring = ring + (size_t)(threadIdx.x >> 5) * ring_stages(CPT) * 32;
   for (long long u = blockIdx.x; u < units; u += gridDim.x) {
-    // frame owning unit u: the last frame whose unit_begin <= u
+    // frame owning unit u: the last of the path's frames whose unit_begin <= u
     int lo = 0, hi = nf - 1;
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
-      if (frames[mid].unit_begin <= u)
+      if (frames[order[mid]].unit_begin <= u)
         lo = mid;
       else
         hi = mid - 1;
     }
-    const TickFrame& fr = frames[lo];
+    const int t = order[lo];
+    const TickFrame& fr = frames[t];
     const SlotParams& sp = a.slots[pushes[fr.push].slot];
     const int local = (int)(u - fr.unit_begin);
     const int b = local / fr.groups_x, g = local - b * fr.groups_x;
     UnitGeom ug;
-    ug.rec = a.recs + lo;
+    ug.rec = a.recs + t;
     ug.depth = fr.depth;
     ug.M = fr.M;
     ug.G = fr.G;
@@ -88,8 +94,8 @@ __global__ void __launch_bounds__(kMapThreads, 2) engine_map_kernel(EngineKernel
     ug.y0 = b * fr.band_h;
     ug.rows = min(fr.band_h, ug.height - ug.y0);
     ug.d0 = sp.d0;
-    ug.gx0 = g * kEngineGroupW;
-    map_unit<kMaxPts, kEngineCPT, TIn, TOut>(ug, Ey, my_ring, P, s_kept);
+    ug.gx0 = g * kGroupW;
+    map_unit<NMAX, CPT, TIn, TOut>(ug, Ey, my_ring, P, s_kept);
   }
 }
 
@@ -102,27 +108,28 @@ __global__ void engine_finalize_kernel(EngineKernelArgs a) {
   finalize_frame(a.recs + t, sp.fp.width, fr.info);
 }
 
-size_t engine_map_smem() { return unit_smem_bytes(kMaxPts, kBandMax, kEngineCPT); }
-
 namespace {
 
-template <typename TIn, typename TOut>
+template <typename TIn, typename TOut, int PATH>
 struct MapKernel {
+  static constexpr int kN = PATH ? kEngineWideNMAX : kMaxPts;
+  static constexpr int kC = PATH ? kEngineWideCPT : kEngineCPT;
+  static size_t smem() { return unit_smem_bytes(kN, kBandMax, kC); }
   static int grid() {
     static int g = 0;
     if (!g) {
-      auto k = engine_map_kernel<TIn, TOut>;
+      auto k = engine_map_kernel<TIn, TOut, kN, kC, PATH>;
       int dev = 0, sms = 0, per = 0;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)engine_map_smem());
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, kMapThreads, engine_map_smem());
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem());
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, kMapThreads, smem());
       g = sms * std::max(per, 1);
     }
     return g;
   }
   static void launch(const EngineKernelArgs& a, int grid, cudaStream_t st) {
-    engine_map_kernel<TIn, TOut><<<grid, kMapThreads, engine_map_smem(), st>>>(a);
+    engine_map_kernel<TIn, TOut, kN, kC, PATH><<<grid, kMapThreads, smem(), st>>>(a);
   }
 };
 
@@ -147,32 +154,45 @@ bool with_types(int din, int dout, F&& f) {
 
 }  // namespace
 
-int engine_map_grid(int din, int dout) {
-  int g = 0;
+EngineGrids engine_map_grids(int din, int dout) {
+  EngineGrids g{};
   with_types(din, dout, [&](auto ti, auto to) {
-    g = MapKernel<decltype(ti), decltype(to)>::grid();
+    g.g[0] = MapKernel<decltype(ti), decltype(to), 0>::grid();
+    g.g[1] = MapKernel<decltype(ti), decltype(to), 1>::grid();
   });
   return g;
 }
 
-cudaError_t launch_engine_map_only(const EngineKernelArgs& a, int din, int dout, int map_grid,
-                                   cudaStream_t st) {
+cudaError_t launch_engine_map_only(const EngineKernelArgs& a, int din, int dout,
+                                   const EngineGrids& grids, cudaStream_t st) {
   if (!with_types(din, dout, [&](auto ti, auto to) {
-        MapKernel<decltype(ti), decltype(to)>::launch(a, map_grid, st);
+        MapKernel<decltype(ti), decltype(to), 0>::launch(a, grids.g[0], st);
+        MapKernel<decltype(ti), decltype(to), 1>::launch(a, grids.g[1], st);
       }))
     return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 
-cudaError_t launch_engine_tick(const EngineKernelArgs& a, int din, int dout, int map_grid,
-                               cudaStream_t st, int64_t* launches) {
+cudaError_t launch_engine_tick(const EngineKernelArgs& a, int din, int dout, const EngineGrids& grids,
+                               cudaStream_t st, const EngineFork& fk, int64_t* launches) {
   const int mf = a.max_frames;
   engine_ingest_kernel<<<(mf + 127) / 128, 128, 0, st>>>(a);
   engine_points_kernel<<<(mf + kEngPtsWarps - 1) / kEngPtsWarps, kEngPtsWarps * 32, 0, st>>>(a);
-  cudaError_t e = launch_engine_map_only(a, din, dout, map_grid, st);
+  cudaError_t e = cudaEventRecord(fk.fork, st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(fk.side, fk.fork, 0);
+  if (e != cudaSuccess) return e;
+  // the two persistent map kernels share the GPU: the tail of one overlaps
+  // the other instead of following it
+  if (!with_types(din, dout, [&](auto ti, auto to) {
+        MapKernel<decltype(ti), decltype(to), 1>::launch(a, grids.g[1], fk.side);
+        MapKernel<decltype(ti), decltype(to), 0>::launch(a, grids.g[0], st);
+      }))
+    return cudaErrorInvalidValue;
+  e = cudaEventRecord(fk.join, fk.side);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, fk.join, 0);
   if (e != cudaSuccess) return e;
   engine_finalize_kernel<<<(mf + 255) / 256, 256, 0, st>>>(a);
-  *launches += 4;
+  *launches += kEngineTickLaunches;
   return cudaGetLastError();
 }
 
