@@ -276,9 +276,19 @@ def run_gpu(args):
                                "planes per stream",
                    "engine_f32": run_batched(torch, mf, dev, args, pools32, torch.float32),
                    "engine_bf16": run_batched(torch, mf, dev, args, pools16, torch.bfloat16),
-                   "plain_f32": run_batched(torch, mf, dev, args, pools32, torch.float32, plain=True)}
+                   "plain_f32": run_batched(torch, mf, dev, args, pools32, torch.float32, plain=True),
+                   # HEADING keeps the motion points in view, so every unit computes and
+                   # reads depth (the ACCEL walkers' points mostly leave the images)
+                   "engine_f32_heading": run_batched(torch, mf, dev, args, pools32, torch.float32,
+                                                     mode="heading"),
+                   "engine_bf16_heading": run_batched(torch, mf, dev, args, pools16, torch.bfloat16,
+                                                      mode="heading"),
+                   "plain_f32_heading": run_batched(torch, mf, dev, args, pools32, torch.float32,
+                                                    plain=True, mode="heading")}
         for k in ("engine_f32", "engine_bf16"):
             batched[k]["vs_plain_f32"] = round(batched[k]["value"] / batched["plain_f32"]["value"], 3)
+            batched[k + "_heading"]["vs_plain_f32"] = round(
+                batched[k + "_heading"]["value"] / batched["plain_f32_heading"]["value"], 3)
         if not args.no_served:
             served = {"workload": "Poisson arrivals 4/s of 30 fps streams (mean 32 s), 128 live "
                                   "at start, cap 256, mixed resolutions, admission by memory "
@@ -447,7 +457,7 @@ def depth_pools(torch, dev, planes, dtype):
     return pools
 
 
-def run_batched(torch, mf, dev, args, pools, dtype, plain=False):
+def run_batched(torch, mf, dev, args, pools, dtype, plain=False, mode="accel"):
     """64 mixed streams (640x480 .. 3840x2160, windows 8..32): every step
     pushes F frames of every stream; engine ticks or plain per-stream calls."""
     from synth import mixed_streams
@@ -475,6 +485,7 @@ def run_batched(torch, mf, dev, args, pools, dtype, plain=False):
         handles = []
         for s in streams:
             h = mf.MotionFocusStream(s["w"], s["h"], window=s["win"], smooth_len=SMOOTH, device=dev,
+                                     mode=mode,
                                      cuda_stream=st, depth_dtype=dtype, map_dtype=dtype,
                                      max_pending=F)
             s["poses_dev"] = torch.from_numpy(s["poses"]).to(dev)
@@ -488,7 +499,8 @@ def run_batched(torch, mf, dev, args, pools, dtype, plain=False):
         eng = mf.MotionFocusEngine(max_streams=n_streams, max_tick_frames=n_streams * F,
                                    max_stream_frames=F, depth_dtype=dtype, map_dtype=dtype,
                                    device=dev, cuda_stream=st, tune=not args.no_tune)
-        slots = [eng.add_stream(s["w"], s["h"], window=s["win"], smooth_len=SMOOTH) for s in streams]
+        slots = [eng.add_stream(s["w"], s["h"], window=s["win"], smooth_len=SMOOTH, mode=mode)
+                 for s in streams]
         rec = np.zeros(n_streams, dtype=mf.PUSH_DTYPE)
         rec["slot"] = slots
         rec["n"] = F
