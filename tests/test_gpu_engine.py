@@ -59,8 +59,9 @@ def _inputs(spec):
     return poses, depth, K
 
 
-def _run_engine(mf, specs, chunk=7, graph=True, tune=True, only=None):
-    """Feed each stream in chunks, one push per stream per tick; returns per-stream outputs."""
+def _run_engine(mf, specs, chunk=7, graph=True, tune=True, only=None, offset=0):
+    """Feed each stream in chunks, one push per stream per tick; returns per-stream outputs.
+    `offset` shifts every plane buffer by that many elements (alignment tests)."""
     dev = torch.device("cuda", 0)
     eng = mf.MotionFocusEngine(max_streams=8, max_tick_frames=512, max_stream_frames=16,
                                graph=graph, tune=tune, device=dev)
@@ -72,10 +73,17 @@ def _run_engine(mf, specs, chunk=7, graph=True, tune=True, only=None):
         width, height, window, smooth_len, mode, seed, frames = spec
         poses, depth, K = _inputs(spec)
         slot = eng.add_stream(width, height, window=window, smooth_len=smooth_len, mode=mode)
-        M = torch.zeros((frames, height, width), device=dev)
-        G = torch.zeros_like(M)
+
+        def planes(data=None):
+            n = frames * height * width
+            buf = torch.zeros(n + offset, device=dev)
+            if data is not None:
+                buf[offset:] = torch.from_numpy(data).reshape(-1).to(dev)
+            return buf[offset:].view(frames, height, width)
+
+        M, G = planes(), planes()
         info = torch.zeros(frames * 64, dtype=torch.uint8, device=dev)
-        state.append(dict(slot=slot, poses=poses, depth=torch.from_numpy(depth).to(dev), K=K,
+        state.append(dict(slot=slot, poses=poses, depth=planes(depth), K=K,
                           M=M, G=G, info=info, next=0, frames=frames))
     ticks = []
     while any(s is not None and s["next"] < s["frames"] for s in state):
@@ -119,6 +127,27 @@ def test_engine_mixed_streams_match_oracle(mf):
             parity.check_map(G[n], Gr, where=f"{spec} G {n}")
             parity.check_argmax(info[n], Mr, rinfo["n_valid"], where=f"{spec} argmax {n}")
         assert info["n_valid"].sum() > 0
+
+
+def test_engine_planes_aligned_to_two_elements_take_the_32_point_path(mf):
+    """Planes shifted by two FP32 elements (8-byte aligned) cannot take the
+    4-pixels-per-lane path: the engine renders those pushes on the 32-point
+    path, within the oracle tolerance, and no wide-path fault or misread."""
+    specs = [STREAMS[0], STREAMS[4]]      # both wide-path streams when aligned
+    outs, _ = _run_engine(mf, specs, offset=2)
+    ref_outs, _ = _run_engine(mf, specs)
+    for spec, (M, G, info), (Ma, Ga, infoa) in zip(specs, outs, ref_outs):
+        width, height, window, smooth_len, mode, seed, frames = spec
+        poses, depth, K = _inputs(spec)
+        ref = O.OracleStream(O.Params(width, height, window=window, smooth_len=smooth_len,
+                                      mode=O.MODE_ACCEL if mode == "accel" else O.MODE_HEADING))
+        ref.push(poses, depth.astype(np.float64), K)
+        for n in range(frames):
+            _, _, Mr, Gr = ref.frame(n)
+            parity.check_map(M[n], Mr, where=f"{spec} M {n}")
+            parity.check_map(G[n], Gr, where=f"{spec} G {n}")
+        for k in parity.INT_FIELDS:
+            assert np.array_equal(info[k], infoa[k]), k
 
 
 def test_engine_alone_and_mixed_identical(mf):
