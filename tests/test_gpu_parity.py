@@ -183,6 +183,22 @@ def test_ragged_and_tiny_frames(mf, width, height, kernel):
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("width,height", [(16384, 6), (6, 16384)])
+def test_largest_dimension(mf, width, height, kernel):
+    """Frames at MF_MAX_DIM in one dimension: 256 column strips of the
+    tensor-core kernel, 16 groups of strips / 64 bands of the CUDA cores."""
+    poses = _accelerating_walk(12)
+    rng = np.random.default_rng(3)
+    depth = rng.uniform(0.2, 5.0, (12, height, width)).astype(np.float32)
+    f = 0.8 * max(width, height)
+    K = np.array([f, f, (width - 1) / 2, (height - 1) / 2])
+    M, G, info, pts, ref = run_both(mf, poses, depth, K, width, height, window=6,
+                                    smooth_len=5, mode="heading", map_kernel=kernel)
+    compare_all(M, G, info, pts, ref, K)
+    assert info["n_valid"].sum() > 0
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
 def test_calibration_rescale(mf, kernel):
     """Intrinsics at twice the map resolution; no depth pushed (G = 0)."""
     poses = _accelerating_walk(40)
