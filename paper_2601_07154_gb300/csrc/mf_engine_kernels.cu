@@ -59,6 +59,8 @@ __global__ void __launch_bounds__(kMapThreads, 2) engine_map_kernel(EngineKernel
   extern __shared__ float4 smem4[];
   __shared__ PointsSmem<kMaxPts> P;
   __shared__ int s_kept;
+  __shared__ uint4 zeros[kZeroBytes / 16];
+  init_zero_source(zeros);
   constexpr int kGroupW = 8 * 32 * CPT;
   const TickHeader* tab = a.table;
   const int nf = tab->n_frames_path[PATH];
@@ -95,8 +97,9 @@ __global__ void __launch_bounds__(kMapThreads, 2) engine_map_kernel(EngineKernel
     ug.rows = min(fr.band_h, ug.height - ug.y0);
     ug.d0 = sp.d0;
     ug.gx0 = g * kGroupW;
-    map_unit<NMAX, CPT, TIn, TOut>(ug, Ey, my_ring, P, s_kept);
+    map_unit<NMAX, CPT, TIn, TOut>(ug, Ey, my_ring, P, s_kept, zeros);
   }
+  bulk_wait_all();
 }
 
 __global__ void engine_finalize_kernel(EngineKernelArgs a) {

@@ -259,6 +259,8 @@ __global__ void __launch_bounds__(kMapThreads, 2) map_stream_kernel(MapParams p,
   uint4* ring = reinterpret_cast<uint4*>(Ey + (size_t)band_h * NMAX);   // [8][stages][32]
   __shared__ PointsSmem<kMaxPts> P;
   __shared__ int s_kept;
+  __shared__ uint4 zeros[kZeroBytes / 16];
+  init_zero_source(zeros);
   constexpr int kGroupW = kGroupStrips * 32 * CPT;
   const int groups_x = (p.width + kGroupW - 1) / kGroupW;
   const int bands = (p.height + band_h - 1) / band_h;
@@ -280,8 +282,9 @@ __global__ void __launch_bounds__(kMapThreads, 2) map_stream_kernel(MapParams p,
     ug.rows = min(band_h, p.height - ug.y0);
     ug.gx0 = g * kGroupW;
     ug.d0 = p.d0;
-    map_unit<NMAX, CPT, TIn, TOut, MODE>(ug, Ey, my_ring, P, s_kept);
+    map_unit<NMAX, CPT, TIn, TOut, MODE>(ug, Ey, my_ring, P, s_kept, zeros);
   }
+  bulk_wait_all();
 }
 
 // ---------------------------------------------------------------------------

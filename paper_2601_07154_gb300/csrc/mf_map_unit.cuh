@@ -94,6 +94,25 @@ __device__ __forceinline__ void cp_async(void* dst, const void* src) {
 
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 
+// Zero rows through the bulk-copy engine: a shared-memory source of zeros,
+// at least one unit row wide (8 strips x 32 lanes x 4 columns x 4 bytes).
+constexpr int kZeroBytes = 8 * 32 * 4 * 4;
+__device__ __forceinline__ void bulk_copy_s2g(void* dst, const void* src_smem, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
+               "r"((uint32_t)__cvta_generic_to_shared(src_smem)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// Every bulk copy this thread issued has written global memory.
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// Fills a kernel's zero source (every thread of the CTA calls this once,
+// before its first unit) and makes it visible to the bulk-copy engine.
+__device__ __forceinline__ void init_zero_source(uint4* zeros) {
+  for (int i = threadIdx.x; i < kZeroBytes / 16; i += blockDim.x) zeros[i] = make_uint4(0u, 0u, 0u, 0u);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
@@ -225,7 +244,7 @@ constexpr int kUnitScaled = 2;
 
 template <int NMAX, int CPT, typename TIn, typename TOut, int MODE = kUnitFull>
 __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* my_ring,
-                                         PointsSmem<kMaxPts>& P, int& s_kept) {
+                                         PointsSmem<kMaxPts>& P, int& s_kept, const uint4* zeros) {
   constexpr int kInBytes = CPT * (int)sizeof(TIn);
   constexpr int kStrip = 32 * CPT;
   constexpr int S = ring_stages(CPT);
@@ -280,15 +299,31 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
   }
   __syncthreads();
   const int nk = s_kept;  // <= NMAX: n never exceeds the window's bucket
-  if (sizeof(TOut) == 2 && nk == 0) {
+  // Zero rows by bulk copy need 16-byte aligned rows in both map planes.
+  const bool bulk = zeros != nullptr && ((size_t)ug.width * sizeof(TOut)) % 16 == 0 &&
+                    ((uintptr_t)ug.M % 16) == 0 && ((uintptr_t)ug.G % 16) == 0;
+  if (nk == 0 && (bulk || sizeof(TOut) == 2)) {
     // No point reaches the unit: M = 0 and G = M min(1, d0/D) = 0 on every
     // pixel, whatever the depth holds, and each lane's maximum is that 0 at
-    // its first pixel.  Zero rows go out with plain stores: no depth copies,
-    // factor tables or per-row bookkeeping.  (Measured on 1080p ACCEL
-    // frames: 16-bit maps gain 5-10 %; FP32 maps, bound by their stores
-    // either way, lose about 1 %, so they keep the general loop below.)
+    // its first pixel.  The zero rows leave through the bulk-copy engine
+    // (one copy per row and map, issued across the CTA), or with 16-bit
+    // maps and unaligned rows through plain stores: no depth copies, factor
+    // tables or per-row bookkeeping.  (Measured on 1080p ACCEL frames: FP32
+    // maps with plain zero stores lose about 1 % against the general loop,
+    // so FP32 without bulk copies keeps that loop.)
+    if (bulk && MODE != kUnitMaxOnly) {
+      const int cols = min(kGroupStrips * kStrip, ug.width - ug.gx0);
+      const uint32_t bytes = (uint32_t)(cols * (int)sizeof(TOut));
+      const size_t first = (size_t)y0 * ug.width + ug.gx0;
+      for (int r = tid; r < rows; r += kMapThreads) {
+        const size_t at = (first + (size_t)r * ug.width) * sizeof(TOut);
+        if (ug.M) bulk_copy_s2g(ug.M + at, zeros, bytes);
+        if (ug.G) bulk_copy_s2g(ug.G + at, zeros, bytes);
+      }
+      bulk_commit();
+    }
     if (x0 >= ug.width) return;  // warp-uniform: this strip lies past the frame
-    if (MODE != kUnitMaxOnly && col_ok) {
+    if (!bulk && MODE != kUnitMaxOnly && col_ok) {
       const float z[CPT] = {};
       const size_t ostride = (size_t)ug.width * sizeof(TOut);
       char* qm = ug.M ? ug.M + row0 * sizeof(TOut) : nullptr;
