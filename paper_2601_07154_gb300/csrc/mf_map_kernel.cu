@@ -463,11 +463,13 @@ cudaError_t launch_n(const MapParams& p, int in_dtype, int out_dtype, bool mx, c
 
 }  // namespace
 
-// The faster kernel as measured on 1080p x 304-frame ACCEL streams
-// (algorithmic bytes over time, as a fraction of measured HBM bandwidth;
-// both kernels skip the depth reads of units no point reaches), CUDA vs
-// tensor cores: FP32 maps, windows 8 / 16 / 32: 1.13 / 1.03 / 0.94 vs
-// 1.10 / 1.03 / 0.67; 16-bit maps: 0.83 / 0.72 / 0.48 vs 0.61 / 0.56 / 0.52.
+// The faster kernel as measured on 1080p x 304-frame streams (algorithmic
+// bytes over time, as a fraction of measured HBM bandwidth), CUDA vs tensor
+// cores, windows 8 / 16 / 32:
+//   ACCEL   FP32   1.15 / 1.04 / 0.95  vs  1.11 / 1.03 / 0.67
+//   ACCEL   16-bit 0.94 / 0.73 / 0.51  vs  0.61 / 0.56 / 0.52
+//   HEADING FP32   0.94 / 0.90 / 0.69  vs  0.90 / 0.91 / 0.48
+//   HEADING 16-bit 0.66 / 0.56 / 0.34  vs  0.49 / 0.44 / 0.37
 bool map_uses_tensor_cores(int path, int window, int map_dtype) {
   if (path == kMapTensorCores) return true;
   if (path == kMapCudaCores) return false;
