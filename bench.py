@@ -432,7 +432,8 @@ def run_e2e(torch, mf, w, depth_dev, dev, args):
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "host_link_gbs": round((h2d + d2h) * n / dt / 1e9, 1),
             "push_call_ms": round(1000 * t_push[0] / n, 2),
-            "step_ms_min_max": [round(float(laps.min()), 2), round(float(laps.max()), 2)],
+            "step_ms_min_median_max": [round(float(laps.min()), 2), round(float(np.median(laps)), 2),
+                                       round(float(laps.max()), 2)],
             "path": "pinned host depth/maps; uploads and downloads on two copy streams in "
                     f"pieces of {PIECE_FRAMES} frames, overlapped with the map kernels"}
 
