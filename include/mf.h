@@ -91,9 +91,9 @@ typedef enum { MF_NORM_COUNT = 0, MF_NORM_MAX = 1 } mf_norm;
  * column factor tables, so it can run on the CUDA cores (one FMA per point
  * and pixel) or on the tensor cores (tcgen05 with TMEM accumulators, three
  * TF32 products per FP32 term).  By default the library takes the faster
- * one as measured on GB300: the tensor cores for 16-bit maps with windows
- * above 16 points, the CUDA cores otherwise.  These flags force one of
- * them (not both). */
+ * one as measured on GB300: the tensor cores for FP32 maps with windows of
+ * up to 16 points and Z = the point count, the CUDA cores otherwise.  These
+ * flags force one of them (not both). */
 #define MF_FLAG_MAP_CUDA_CORES 8u
 #define MF_FLAG_MAP_TENSOR_CORES 16u
 
@@ -483,9 +483,9 @@ int mf_server_close(mf_server* s);
  * It computes what a WORLD-pose stream would return for the last n_render of
  * n_poses consecutive poses (frames 0 .. n_poses-1; the earlier poses serve
  * as the window's history), with no mf_stream and no allocation: its
- * scratch (pose copies, rigidity flags, per-frame records, about 560 KB) is
- * a static device array inside libmf that every GPU loading the library
- * holds until the process exits.  The caller passes and owns the inputs and
+ * scratch (pose copies, rigidity flags, per-frame records and a work
+ * counter, about 560 KB) is a static device array inside libmf that every
+ * GPU loading the library holds until the process exits.  The caller passes and owns the inputs and
  * the outputs.
  *   d              stream descriptor: sizes, window, smooth_len, mode,
  *                  dtypes, sigma/s/d0 parameters and cuda_stream are used;

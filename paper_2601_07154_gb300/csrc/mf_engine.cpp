@@ -134,6 +134,7 @@ struct mf_engine {
   int32_t* bad_pool = nullptr;
   int64_t ring_cap = 0;              // poses per slot history
   FrameRec* recs = nullptr;
+  unsigned int* sched = nullptr;  // map paths' work counters (kEnginePaths)
   size_t tab_bytes = 0;
   char* host_tab[2] = {nullptr, nullptr};
   char* dev_tab[2] = {nullptr, nullptr};
@@ -240,6 +241,7 @@ mf::EngineKernelArgs kernel_args(mf_engine* e, int b) {
   a.slots = e->slots_dev;
   a.recs = e->recs;
   a.max_frames = e->d.max_tick_frames;
+  a.sched = e->sched;
   return a;
 }
 
@@ -289,6 +291,7 @@ void destroy(mf_engine* e) {
     if (e->t0[b]) cudaEventDestroy(e->t0[b]);
   }
   e->dfree(e->recs, (size_t)e->d.max_tick_frames * sizeof(FrameRec));
+  e->dfree(e->sched, mf::kEnginePaths * sizeof(unsigned int));
   e->dfree(e->slots_dev, (size_t)(e->d.max_streams + 1) * sizeof(SlotParams));
   if (e->cap_st) cudaStreamDestroy(e->cap_st);
   if (e->fork.side) {
@@ -547,6 +550,13 @@ int mf_engine_open(const mf_engine_desc* d, mf_engine** out) {
     e->slots_pinned = nullptr;
   }
   e->recs = (FrameRec*)e->dalloc((size_t)d->max_tick_frames * sizeof(FrameRec));
+  e->sched = (unsigned int*)e->dalloc(mf::kEnginePaths * sizeof(unsigned int));
+  if (e->sched &&
+      cudaMemsetAsync(e->sched, 0, mf::kEnginePaths * sizeof(unsigned int), e->st) != cudaSuccess) {
+    cudaGetLastError();
+    e->dfree(e->sched, mf::kEnginePaths * sizeof(unsigned int));
+    e->sched = nullptr;
+  }
   e->tab_bytes = table_bytes(d->max_tick_frames, d->max_streams, e->poses_cap());
   for (int b = 0; b < 2; ++b) {
     e->dev_tab[b] = (char*)e->dalloc(e->tab_bytes);
@@ -556,7 +566,7 @@ int mf_engine_open(const mf_engine_desc* d, mf_engine** out) {
     }
     if (cudaEventCreateWithFlags(&e->done[b], cudaEventDisableTiming) != cudaSuccess) e->done[b] = nullptr;
   }
-  if (!e->slots_dev || !e->ring_pool || !e->bad_pool || !e->slots_pinned || !e->recs ||
+  if (!e->slots_dev || !e->ring_pool || !e->bad_pool || !e->slots_pinned || !e->recs || !e->sched ||
       !e->dev_tab[0] || !e->dev_tab[1] || !e->host_tab[0] ||
       !e->host_tab[1] || !e->done[0] || !e->done[1]) {
     destroy(e);

@@ -77,6 +77,9 @@ struct EngineKernelArgs {
   const SlotParams* slots;     // device slot parameters
   FrameRec* recs;              // max_tick_frames records
   int max_frames;              // capacity (grid sizes of the per-frame kernels)
+  // one work counter per map path for the dynamic unit schedule (0 between
+  // launches; the two paths run concurrently, so each has its own)
+  unsigned int* sched;         // [kEnginePaths]
 };
 
 // Kernel launches of one tick: ingest, points, the two map paths, finalize.

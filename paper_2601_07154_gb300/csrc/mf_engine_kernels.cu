@@ -70,8 +70,11 @@ __global__ void __launch_bounds__(kMapThreads, 2) engine_map_kernel(EngineKernel
   const TickPush* pushes = tick_pushes(tab);
   float* Ey = reinterpret_cast<float*>(smem4);
   uint4* ring = reinterpret_cast<uint4*>(Ey + (size_t)kBandMax * NMAX);
-  uint4* my_ring = ring + (size_t)(threadIdx.x >> 5) * ring_stages(CPT) * 32;
-  for (long long u = blockIdx.x; u < units; u += gridDim.x) {
+  uint4* my_ring = ring + (size_t)(threadIdx.x >> 5) * ring_stages(CPT, (int)sizeof(TIn)) * 32;
+  __shared__ long long s_next[2];
+  long long u = blockIdx.x;
+  for (int k = 0; u < units; ++k) {
+    const unsigned claim = claim_unit(a.sched + PATH);
     // frame owning unit u: the last of the path's frames whose unit_begin <= u
     int lo = 0, hi = nf - 1;
     while (lo < hi) {
@@ -98,6 +101,7 @@ __global__ void __launch_bounds__(kMapThreads, 2) engine_map_kernel(EngineKernel
     ug.d0 = sp.d0;
     ug.gx0 = g * kGroupW;
     map_unit<NMAX, CPT, TIn, TOut>(ug, Ey, my_ring, P, s_kept, zeros);
+    u = next_unit(a.sched + PATH, claim, units, s_next, k);
   }
   bulk_wait_all();
 }
@@ -117,7 +121,7 @@ template <typename TIn, typename TOut, int PATH>
 struct MapKernel {
   static constexpr int kN = PATH ? kEngineWideNMAX : kMaxPts;
   static constexpr int kC = PATH ? kEngineWideCPT : kEngineCPT;
-  static size_t smem() { return unit_smem_bytes(kN, kBandMax, kC); }
+  static size_t smem() { return unit_smem_bytes(kN, kBandMax, kC, (int)sizeof(TIn)); }
   static int grid() {
     static int g = 0;
     if (!g) {

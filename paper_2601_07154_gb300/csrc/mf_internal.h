@@ -85,6 +85,9 @@ struct MapParams {
   void* G;                 // (may be NULL)
   float d0;
   int path;                // kMapAuto, kMapCudaCores or kMapTensorCores
+  // Work counter of the persistent map kernels' dynamic unit schedule: 0 at
+  // launch and left at 0; no two launches in flight may share it.
+  unsigned int* sched;
 };
 
 // MF_NORM_MAX applies to frames whose count-normalised map maximum is at
@@ -122,8 +125,9 @@ struct NormalizeParams {
 // the number of kernels launched.
 cudaError_t launch_ingest(const IngestParams& p, cudaStream_t st, int64_t* launches);
 cudaError_t launch_points(const PointsParams& p, cudaStream_t st, int64_t* launches);
-// Which map kernel launch_map runs for a launch path, window and map type.
-bool map_uses_tensor_cores(int path, int window, int map_dtype);
+// Which map kernel launch_map runs for a launch path, window, map type and
+// normalisation.
+bool map_uses_tensor_cores(int path, int window, int map_dtype, int normalize);
 // Tensor-core map kernel (mf_map_tc.cu); any width, any plane alignment.
 cudaError_t launch_map_tc(const MapParams& p, int window, int depth_dtype, int map_dtype,
                           cudaStream_t st, int64_t* launches);

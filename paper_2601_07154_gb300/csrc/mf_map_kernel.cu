@@ -250,8 +250,9 @@ __global__ void __launch_bounds__(kMapThreads) map_kernel(MapParams p) {
 
 // ---------------------------------------------------------------------------
 // Streaming kernel for frames whose rows allow CPT-pixel vector access (the
-// common case): persistent CTAs of 8 warps walk the frames' units (band of
-// up to 256 rows x group of 8 strips) in frame order; map_unit does the work.
+// common case): persistent CTAs of 8 warps take the frames' units (band of
+// up to 256 rows x group of 8 strips) in frame order from the dynamic
+// schedule; map_unit does the work.
 template <int NMAX, int CPT, typename TIn, typename TOut, int MODE>
 __global__ void __launch_bounds__(kMapThreads, 2) map_stream_kernel(MapParams p, int band_h) {
   extern __shared__ float4 smem4[];
@@ -266,8 +267,11 @@ __global__ void __launch_bounds__(kMapThreads, 2) map_stream_kernel(MapParams p,
   const int bands = (p.height + band_h - 1) / band_h;
   const long long units = (long long)p.n_frames * bands * groups_x;
   const size_t plane = (size_t)p.width * (size_t)p.height;
-  uint4* my_ring = ring + (size_t)(threadIdx.x >> 5) * ring_stages(CPT) * 32;
-  for (long long u = blockIdx.x; u < units; u += gridDim.x) {
+  uint4* my_ring = ring + (size_t)(threadIdx.x >> 5) * ring_stages(CPT, (int)sizeof(TIn)) * 32;
+  __shared__ long long s_next[2];
+  long long u = blockIdx.x;
+  for (int k = 0; u < units; ++k) {
+    const unsigned claim = claim_unit(p.sched);
     const int f = (int)(u / ((long long)bands * groups_x));
     const int rem = (int)(u - (long long)f * bands * groups_x);
     const int b = rem / groups_x, g = rem - b * groups_x;
@@ -283,6 +287,7 @@ __global__ void __launch_bounds__(kMapThreads, 2) map_stream_kernel(MapParams p,
     ug.gx0 = g * kGroupW;
     ug.d0 = p.d0;
     map_unit<NMAX, CPT, TIn, TOut, MODE>(ug, Ey, my_ring, P, s_kept, zeros);
+    u = next_unit(p.sched, claim, units, s_next, k);
   }
   bulk_wait_all();
 }
@@ -415,7 +420,8 @@ cudaError_t launch_typed(const MapParams& p, bool norm_max, cudaStream_t st, int
     constexpr int kGroupW = kGroupStrips * 32 * CPT;
     const long long units =
         (long long)p.n_frames * bands * ((p.width + kGroupW - 1) / kGroupW);
-    const size_t smem_max = unit_smem_bytes(NMAX, kBandMax, CPT), smem = unit_smem_bytes(NMAX, band_h, CPT);
+    const size_t smem_max = unit_smem_bytes(NMAX, kBandMax, CPT, (int)sizeof(TIn)),
+                 smem = unit_smem_bytes(NMAX, band_h, CPT, (int)sizeof(TIn));
     static int per_sm[3] = {-1, -1, -1}, sms = 0;
     if (!norm_max) {
       launch_persistent(map_stream_kernel<NMAX, CPT, TIn, TOut, kUnitFull>, &per_sm[0], &sms,
@@ -466,21 +472,25 @@ cudaError_t launch_n(const MapParams& p, int in_dtype, int out_dtype, bool mx, c
 // The faster kernel as measured on 1080p x 304-frame streams (algorithmic
 // bytes over time, as a fraction of measured HBM bandwidth), CUDA vs tensor
 // cores, windows 8 / 16 / 32:
-//   ACCEL   FP32   1.15 / 1.04 / 0.95  vs  1.11 / 1.03 / 0.67
-//   ACCEL   16-bit 0.94 / 0.73 / 0.51  vs  0.61 / 0.56 / 0.52
-//   HEADING FP32   0.94 / 0.90 / 0.69  vs  0.90 / 0.91 / 0.48
-//   HEADING 16-bit 0.66 / 0.56 / 0.34  vs  0.49 / 0.44 / 0.37
-bool map_uses_tensor_cores(int path, int window, int map_dtype) {
+//   ACCEL   FP32   1.20 / 1.11 / 1.01  vs  1.25 / 1.16 / 0.69
+//   ACCEL   16-bit 1.11 / 0.97 / 0.59  vs  0.65 / 0.60 / 0.54
+//   HEADING FP32   0.95 / 0.91 / 0.71  vs  0.99 / 0.92 / 0.48
+//   HEADING 16-bit 0.74 / 0.61 / 0.35  vs  0.51 / 0.45 / 0.39
+// (1080p x 900 frames, ACCEL FP32, window 16: 1.09 vs 1.13.)  With Z = the
+// map maximum the CUDA-core kernel finds the maxima in a pass without
+// memory traffic and scales while it writes, where the tensor-core kernel
+// needs another read-and-write pass over both maps.
+bool map_uses_tensor_cores(int path, int window, int map_dtype, int normalize) {
   if (path == kMapTensorCores) return true;
   if (path == kMapCudaCores) return false;
-  return map_dtype != MF_F32 && window > 16;
+  return map_dtype == MF_F32 && window <= 16 && normalize != MF_NORM_MAX;
 }
 
 cudaError_t launch_map(const MapParams& p, int window, int in_dtype, int out_dtype, int normalize,
                        cudaStream_t st, int64_t* launches) {
   if (p.n_frames <= 0) return cudaSuccess;
   const bool mx = normalize == MF_NORM_MAX;
-  if (map_uses_tensor_cores(p.path, window, out_dtype)) {
+  if (map_uses_tensor_cores(p.path, window, out_dtype, normalize)) {
     cudaError_t e = launch_map_tc(p, window, in_dtype, out_dtype, st, launches);
     if (e == cudaSuccess && mx) e = launch_normalize(normalize_params(p), out_dtype, st, launches);
     return e;

@@ -13,14 +13,15 @@
 // rounded up to 8), so one tcgen05.mma chain of K'/8 steps per tile computes
 // the tile in TMEM with FP32 accumulation:
 //     A (M = 128 columns x K') = [Ex_hi | Ex_hi | Ex_lo],
-//     B (N = 128 rows    x K') = [Ey_hi | Ey_lo | Ey_hi],
+//     B (N = 64 rows     x K') = [Ey_hi | Ey_lo | Ey_hi],
 //     D[x][y] = sum_k A[x][k] B[y][k]   (TMEM lane = column, TMEM column = row).
 // With lane = column, each warp's epilogue reads one row of 32 adjacent
 // columns per TMEM column, so depth loads and map stores are coalesced.
 //
-// Work item = one strip of 128 columns of one frame, all bands of 128 rows:
-// A is built once per item (column factors of the points kept for the
-// strip), B once per band.  One elected thread issues the MMAs and commits
+// Work item = one strip of 128 columns of one frame, all bands of 64 rows;
+// CTAs take items from the map kernels' dynamic schedule.  A is built once
+// per item (column factors of the points kept for the strip), B once per
+// band.  One elected thread issues the MMAs and commits
 // them to an mbarrier that the epilogue waits on (bounded; a wait that runs
 // out poisons the band's maps with NaN rather than hang).  Operands live in
 // shared memory in the no-swizzle K-major core-matrix layout (8 rows x 16 B
@@ -256,7 +257,11 @@ __global__ void __launch_bounds__(kTcThreads, 2) map_tc_kernel(MapParams p, int 
   const int bands = (p.height + kTcRows - 1) / kTcRows;
   const int items = p.n_frames * strips;
 
-  for (int item = blockIdx.x; item < items; item += gridDim.x) {
+  __shared__ long long s_next[2];
+  long long next = blockIdx.x;
+  for (int k = 0; next < items; ++k) {
+    const int item = (int)next;
+    const unsigned claim = claim_unit(p.sched);
     const int f = item / strips;
     const int gx0 = (item - f * strips) * kTcCols;
     const int gx1 = min(p.width, gx0 + kTcCols) - 1;
@@ -393,6 +398,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) map_tc_kernel(MapParams p, int 
       key = k2 > key ? k2 : key;
     }
     if (lane == 0 && n > 0 && key) atomicMax(const_cast<unsigned long long*>(&rec->argmax_key), key);
+    next = next_unit(p.sched, claim, items, s_next, k);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -438,6 +444,7 @@ cudaError_t launch_tc_typed(const MapParams& p, int kk_max, cudaStream_t st) {
   const int strips = (p.width + kTcCols - 1) / kTcCols;
   const long long items = (long long)p.n_frames * strips;
   const long long grid = std::min<long long>(items, (long long)per_sm[slot] * sms);
+  if (items > 0x7fffffffLL) return cudaErrorInvalidConfiguration;  // item indices are int
   k<<<(unsigned)grid, kTcThreads, smem, st>>>(p, strips, kk_max);
   return cudaGetLastError();
 }

@@ -32,9 +32,10 @@ namespace mf {
 
 constexpr float kCullBelow = 9.094947017729282e-13f;  // 2^-40
 
-// Depth rows in flight per warp: lanes reading 2 pixels per row need twice
-// the stages to keep the same bytes in flight.
-__host__ __device__ constexpr int ring_stages(int cpt) { return cpt >= 4 ? kStages : 2 * kStages; }
+// Depth rows in flight per warp: kStages rows of 16 bytes per lane, and
+// proportionally more rows where a lane reads fewer bytes per row (2 pixels,
+// or 16-bit depth), so every ring holds the same bytes in flight.
+__host__ __device__ constexpr int ring_stages(int cpt, int in_bytes) { return kStages * 16 / (cpt * in_bytes); }
 
 template <int NMAX>
 struct PointsSmem {
@@ -247,7 +248,7 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
                                          PointsSmem<kMaxPts>& P, int& s_kept, const uint4* zeros) {
   constexpr int kInBytes = CPT * (int)sizeof(TIn);
   constexpr int kStrip = 32 * CPT;
-  constexpr int S = ring_stages(CPT);
+  constexpr int S = ring_stages(CPT, (int)sizeof(TIn));
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int rows = ug.rows, y0 = ug.y0;
   const int x0 = ug.gx0 + warp * kStrip;
@@ -478,9 +479,36 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
 }
 
 // Dynamic shared memory of a CTA running units of bucket NMAX with CPT
-// pixels per lane: the band's row factors, then every warp's depth ring.
-__host__ __device__ constexpr size_t unit_smem_bytes(int nmax, int band_h, int cpt) {
-  return (size_t)band_h * nmax * 4 + (size_t)(kMapThreads / 32) * ring_stages(cpt) * 32 * 16;
+// pixels per lane and in_bytes-byte depth: the band's row factors, then
+// every warp's depth ring.
+__host__ __device__ constexpr size_t unit_smem_bytes(int nmax, int band_h, int cpt, int in_bytes) {
+  return (size_t)band_h * nmax * 4 + (size_t)(kMapThreads / 32) * ring_stages(cpt, in_bytes) * 32 * 16;
+}
+
+// Dynamic unit schedule of the persistent map kernels.  CTA c starts on
+// unit c.  While the CTA works on a unit, its thread 0 holds a claim on the
+// next one from a launch-wide counter (claims at or past the last unit end
+// the CTA's loop), so CTAs that draw cheap units -- ones no point reaches --
+// take more of them instead of idling at the end of the launch.  Every unit
+// processed makes one claim, so a launch makes exactly `units` of them and
+// the claim that returns units - 1 is its last: that thread puts the counter
+// back to 0 for the next launch.  The counter must be 0 at launch, and no
+// two launches in flight may share it; a launch holds fewer than 2^32 units.
+__device__ __forceinline__ unsigned claim_unit(unsigned* ctr) {
+  return threadIdx.x == 0 ? atomicAdd(ctr, 1u) : 0u;
+}
+
+// Called by every thread after the CTA's k-th unit with thread 0's claim:
+// the CTA's next unit.  s_next is two shared slots, so a slow thread
+// still reading slot k & 1 never sees the write of claim k + 1.
+__device__ __forceinline__ long long next_unit(unsigned* ctr, unsigned claim, long long units,
+                                               long long* s_next, int k) {
+  if (threadIdx.x == 0) {
+    s_next[k & 1] = (long long)gridDim.x + (long long)claim;
+    if ((long long)claim == units - 1) *ctr = 0u;  // the launch's last claim
+  }
+  __syncthreads();
+  return s_next[k & 1];
 }
 
 }  // namespace mf

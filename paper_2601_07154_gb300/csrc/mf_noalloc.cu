@@ -26,9 +26,12 @@ constexpr size_t kRecBytes = sizeof(mf::FrameRec) * kRecSlots;
 constexpr size_t kPoseOff = (kRecBytes + 255) / 256 * 256;
 constexpr size_t kPoseBytes = sizeof(double) * 12 * kRingSlots;
 constexpr size_t kBadOff = kPoseOff + (kPoseBytes + 255) / 256 * 256;
-constexpr size_t kScratchBytes = kBadOff + sizeof(int32_t) * kRingSlots;
+constexpr size_t kSchedOff = kBadOff + (sizeof(int32_t) * kRingSlots + 255) / 256 * 256;
+constexpr size_t kScratchBytes = kSchedOff + sizeof(unsigned int);
 
-// The shared scratch: frame records, then pose copies, then rigidity flags.
+// The shared scratch: frame records, then pose copies, then rigidity flags,
+// then the map kernels' work counter (zero from load, and every map launch
+// leaves it at zero).
 static __device__ __align__(256) unsigned char mf_noalloc_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
@@ -102,6 +105,7 @@ extern "C" int mf_render_noalloc(const mf_stream_desc* d, int32_t n_poses,
   mf::FrameRec* recs = reinterpret_cast<mf::FrameRec*>(scratch);
   double* ring = reinterpret_cast<double*>(scratch + kPoseOff);
   int32_t* bad = reinterpret_cast<int32_t*>(scratch + kBadOff);
+  unsigned int* sched = reinterpret_cast<unsigned int*>(scratch + kSchedOff);
   cudaStream_t st = static_cast<cudaStream_t>(d->cuda_stream);
   int64_t launches = 0;
 
@@ -157,6 +161,7 @@ extern "C" int mf_render_noalloc(const mf_stream_desc* d, int32_t n_poses,
     mp.G = guided_depth;
     mp.d0 = (float)d->depth_ref_m;
     mp.path = mf::host_map_path(d->flags);
+    mp.sched = sched;
     e = mf::launch_map(mp, d->window, d->depth_dtype, d->map_dtype, d->normalize, st, &launches);
   }
   if (e == cudaSuccess && info) {

@@ -202,6 +202,7 @@ struct mf_stream {
   int64_t ring_cap = 0;
   FrameRec* recs = nullptr;
   int64_t rec_cap = 0;
+  unsigned int* sched = nullptr;  // map kernels' work counter
 
   double* pose_dev = nullptr;      // device staging of host poses
   int64_t pose_dev_cap = 0;
@@ -432,6 +433,7 @@ void destroy(mf_stream* s) {
   s->dfree(s->ring, (size_t)s->ring_cap * 12 * sizeof(double));
   s->dfree(s->ring_bad, (size_t)s->ring_cap * sizeof(int32_t));
   s->dfree(s->recs, (size_t)s->rec_cap * sizeof(FrameRec));
+  s->dfree(s->sched, sizeof(unsigned int));
   s->dfree(s->pose_dev, (size_t)s->pose_dev_cap * 12 * sizeof(double));
   s->dfree(s->stage, (size_t)s->stage_slots * s->plane_in);
   s->dfree(s->out_stage, s->out_stage_bytes);
@@ -552,9 +554,16 @@ int mf_open_stream(const mf_stream_desc* d, mf_stream** out) {
   }
   s->rec_cap = pow2_at_least(d->max_pending);
   s->recs = (FrameRec*)s->dalloc((size_t)s->rec_cap * sizeof(FrameRec));
-  if (!s->recs) {
+  s->sched = (unsigned int*)s->dalloc(sizeof(unsigned int));
+  if (!s->recs || !s->sched) {
     destroy(s);
     return fail(MF_ERR_OOM, "frame record allocation failed");
+  }
+  // every map launch of the stream leaves its counter at 0 again
+  if (cudaMemsetAsync(s->sched, 0, sizeof(unsigned int), s->st) != cudaSuccess) {
+    cudaGetLastError();
+    destroy(s);
+    return fail(MF_ERR_CUDA, "work counter initialisation failed");
   }
   rc = grow_ring(s, d->window + d->smooth_len + 64);
   if (rc) {
@@ -805,6 +814,7 @@ int mf_get_maps(mf_stream* s, int32_t max_frames, void* focus_map, void* guided_
     mp.G = Gp;
     mp.d0 = (float)s->d.depth_ref_m;
     mp.path = map_path(s->d.flags);
+    mp.sched = s->sched;
     TimerPair tp{};
     if (timed) {
       rc = timer_pair(s, &tp);
@@ -814,7 +824,7 @@ int mf_get_maps(mf_stream* s, int32_t max_frames, void* focus_map, void* guided_
     MF_CUDA(mf::launch_map(mp, s->d.window, s->d.depth_dtype, s->d.map_dtype, s->d.normalize, s->st,
                            &s->launches),
             "map launch");
-    s->last_map_kernel = mf::map_uses_tensor_cores(mp.path, s->d.window, s->d.map_dtype)
+    s->last_map_kernel = mf::map_uses_tensor_cores(mp.path, s->d.window, s->d.map_dtype, s->d.normalize)
                              ? MF_FLAG_MAP_TENSOR_CORES
                              : MF_FLAG_MAP_CUDA_CORES;
     if (timed) {
