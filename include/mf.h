@@ -90,10 +90,10 @@ typedef enum { MF_NORM_COUNT = 0, MF_NORM_MAX = 1 } mf_norm;
 /* Map kernel choice.  Eq. 7 over a tile is a rank-N product of row and
  * column factor tables, so it can run on the CUDA cores (one FMA per point
  * and pixel) or on the tensor cores (tcgen05 with TMEM accumulators, three
- * TF32 products per FP32 term).  By default the library takes the faster
- * one as measured on GB300: the tensor cores for FP32 maps with windows of
- * up to 16 points and Z = the point count, the CUDA cores otherwise.  These
- * flags force one of them (not both). */
+ * TF32 products per FP32 term).  The map is HBM-bound, not a dense
+ * contraction, so the library runs the CUDA-core kernel unless
+ * MF_FLAG_MAP_TENSOR_CORES asks for the tensor cores; MF_FLAG_MAP_CUDA_CORES
+ * names the default explicitly.  The flags are exclusive. */
 #define MF_FLAG_MAP_CUDA_CORES 8u
 #define MF_FLAG_MAP_TENSOR_CORES 16u
 

@@ -125,9 +125,8 @@ struct NormalizeParams {
 // the number of kernels launched.
 cudaError_t launch_ingest(const IngestParams& p, cudaStream_t st, int64_t* launches);
 cudaError_t launch_points(const PointsParams& p, cudaStream_t st, int64_t* launches);
-// Which map kernel launch_map runs for a launch path, window, map type and
-// normalisation.
-bool map_uses_tensor_cores(int path, int window, int map_dtype, int normalize);
+// Whether launch_map runs the tensor-core kernel for a launch path.
+bool map_uses_tensor_cores(int path);
 // Tensor-core map kernel (mf_map_tc.cu); any width, any plane alignment.
 cudaError_t launch_map_tc(const MapParams& p, int window, int depth_dtype, int map_dtype,
                           cudaStream_t st, int64_t* launches);

@@ -469,28 +469,21 @@ cudaError_t launch_n(const MapParams& p, int in_dtype, int out_dtype, bool mx, c
 
 }  // namespace
 
-// The faster kernel as measured on 1080p x 304-frame streams (algorithmic
-// bytes over time, as a fraction of measured HBM bandwidth), CUDA vs tensor
-// cores, windows 8 / 16 / 32:
-//   ACCEL   FP32   1.20 / 1.11 / 1.01  vs  1.25 / 1.16 / 0.69
-//   ACCEL   16-bit 1.11 / 0.97 / 0.59  vs  0.65 / 0.60 / 0.54
-//   HEADING FP32   0.95 / 0.91 / 0.71  vs  0.99 / 0.92 / 0.48
-//   HEADING 16-bit 0.74 / 0.61 / 0.35  vs  0.51 / 0.45 / 0.39
-// (1080p x 900 frames, ACCEL FP32, window 16: 1.09 vs 1.13.)  With Z = the
-// map maximum the CUDA-core kernel finds the maxima in a pass without
-// memory traffic and scales while it writes, where the tensor-core kernel
-// needs another read-and-write pass over both maps.
-bool map_uses_tensor_cores(int path, int window, int map_dtype, int normalize) {
-  if (path == kMapTensorCores) return true;
-  if (path == kMapCudaCores) return false;
-  return map_dtype == MF_F32 && window <= 16 && normalize != MF_NORM_MAX;
-}
+// The map is HBM-bound work (about N FMAs per 12 bytes), so the CUDA-core
+// kernel is the default.  The tensor-core kernel runs only when forced: as
+// a fraction of measured HBM bandwidth (algorithmic bytes, 1080p x 304
+// frames, windows 8 / 16 / 32), CUDA vs tensor cores:
+//   ACCEL   FP32   1.24 / 1.14 / 1.04  vs  1.25 / 1.16 / 0.69
+//   ACCEL   16-bit 1.15 / 1.01 / 0.60  vs  0.65 / 0.60 / 0.54
+//   HEADING FP32   0.95 / 0.91 / 0.73  vs  0.99 / 0.92 / 0.48
+//   HEADING 16-bit 0.74 / 0.59 / 0.36  vs  0.51 / 0.45 / 0.39
+bool map_uses_tensor_cores(int path) { return path == kMapTensorCores; }
 
 cudaError_t launch_map(const MapParams& p, int window, int in_dtype, int out_dtype, int normalize,
                        cudaStream_t st, int64_t* launches) {
   if (p.n_frames <= 0) return cudaSuccess;
   const bool mx = normalize == MF_NORM_MAX;
-  if (map_uses_tensor_cores(p.path, window, out_dtype, normalize)) {
+  if (map_uses_tensor_cores(p.path)) {
     cudaError_t e = launch_map_tc(p, window, in_dtype, out_dtype, st, launches);
     if (e == cudaSuccess && mx) e = launch_normalize(normalize_params(p), out_dtype, st, launches);
     return e;

@@ -11,6 +11,9 @@
 //     (times 1/Z) is below 2^-40 contributes less than 2^-40 to every pixel
 //     of it, far inside the 1e-10 absolute floor of the map tolerance; kept
 //     points keep their order;
+//   * each warp applies the same rule to its own strip: a strip that no
+//     kept point reaches reads no depth and writes zeros (at most 32 points
+//     are dropped from any pixel, each below 2^-40, together below 2^-35);
 //   * the CTA evaluates the band's row factors once in shared memory;
 //   * each warp owns one strip: every lane holds its CPT columns' factors for
 //     the kept points in registers and streams the band's rows two at a time
@@ -348,6 +351,23 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
   // Depth only scales G: with no G output, or no point kept (M = 0, so G = 0
   // whatever D holds), its rows are not read.
   if (nk == 0 || !ug.G) dsrc = nullptr;
+  // A warp whose strip none of the kept points reaches (the same 2^-40 rule
+  // over the strip's columns and the band's rows) has M = 0 and G = 0 there:
+  // it reads no depth and writes zeros.
+  bool strip_zero = false;
+  {
+    const int sx1 = min(ug.width, x0 + kStrip) - 1;
+    bool reach = false;
+    if (lane < nk && x0 <= sx1) {
+      const float xn = fminf(fmaxf(rintf(P.uhi[lane] + P.ulo[lane]), (float)x0), (float)sx1);
+      const float yn = fminf(fmaxf(rintf(P.vhi[lane] + P.vlo[lane]), (float)y0), (float)(y0 + rows - 1));
+      const float peak = gauss_factor(xn, P.uhi[lane], P.ulo[lane], P.chi[lane], P.clo[lane]) *
+                         gauss_factor(yn, P.vhi[lane], P.vlo[lane], P.chi[lane], P.clo[lane]);
+      reach = peak * inv_n >= kCullBelow;
+    }
+    strip_zero = __ballot_sync(0xffffffffu, reach) == 0u;
+  }
+  if (strip_zero) dsrc = nullptr;
   // the first depth rows are in flight while the factors are computed
 #pragma unroll
   for (int s = 0; s < S - 2; ++s) issue(s);
@@ -374,6 +394,39 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
   }
   __syncthreads();  // Ey complete
   if (x0 >= ug.width) return;  // warp-uniform: this strip lies past the frame (no copies issued)
+  if (strip_zero) {
+    if (MODE != kUnitMaxOnly) {
+      if (bulk) {
+        const uint32_t bytes = (uint32_t)(min(kStrip, ug.width - x0) * (int)sizeof(TOut));
+        const size_t first = (size_t)y0 * ug.width + x0;
+        for (int r = lane; r < rows; r += 32) {
+          const size_t at = (first + (size_t)r * ug.width) * sizeof(TOut);
+          if (ug.M) bulk_copy_s2g(ug.M + at, zeros, bytes);
+          if (ug.G) bulk_copy_s2g(ug.G + at, zeros, bytes);
+        }
+        bulk_commit();
+      } else if (col_ok) {
+        const float z[CPT] = {};
+        const size_t ostride = (size_t)ug.width * sizeof(TOut);
+        char* qm = ug.M ? ug.M + row0 * sizeof(TOut) : nullptr;
+        char* qg = ug.G ? ug.G + row0 * sizeof(TOut) : nullptr;
+        for (size_t off = 0, end = (size_t)rows * ostride; off < end; off += ostride) {
+          if (qm) Vec<TOut, CPT>::store(qm + off, 0, z);
+          if (qg) Vec<TOut, CPT>::store(qg + off, 0, z);
+        }
+      }
+    }
+    if (MODE != kUnitScaled) {
+      unsigned long long key =
+          col_ok ? (unsigned long long)(0xffffffffu - (unsigned)(y0 * ug.width + xc)) : 0ull;
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
+        key = k2 > key ? k2 : key;
+      }
+      if (lane == 0 && n > 0 && key) atomicMax(&rec->argmax_key, key);
+    }
+    return;
+  }
 
   float best = -1.0f;
   unsigned bidx = 0;

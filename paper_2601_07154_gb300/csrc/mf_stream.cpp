@@ -824,7 +824,7 @@ int mf_get_maps(mf_stream* s, int32_t max_frames, void* focus_map, void* guided_
     MF_CUDA(mf::launch_map(mp, s->d.window, s->d.depth_dtype, s->d.map_dtype, s->d.normalize, s->st,
                            &s->launches),
             "map launch");
-    s->last_map_kernel = mf::map_uses_tensor_cores(mp.path, s->d.window, s->d.map_dtype, s->d.normalize)
+    s->last_map_kernel = mf::map_uses_tensor_cores(mp.path)
                              ? MF_FLAG_MAP_TENSOR_CORES
                              : MF_FLAG_MAP_CUDA_CORES;
     if (timed) {

@@ -25,8 +25,8 @@ class MotionFocusStream:
     structured arrays (layouts of ``mf_frame_info`` / ``mf_motion_point``).
     ``normalize`` picks Z of Eq. 7: "count" (the number of valid points) or
     "max" (the frame's map maximum, so that every non-empty map peaks at 1).
-    ``map_kernel`` forces the CUDA-core ("cuda_cores") or the tensor-core
-    ("tensor_cores") map kernel; "auto" lets the library choose.
+    ``map_kernel`` picks the CUDA-core ("cuda_cores", also what "auto"
+    runs) or the tensor-core ("tensor_cores") map kernel.
     """
 
     def __init__(self, width, height, window=8, smooth_len=15, mode="accel",
