@@ -112,12 +112,17 @@ struct Slot {
   int band_h = 0, bands = 0, groups_x = 0;
 };
 
-// Columns per map unit of a path.
-int path_group_w(int path) { return path ? mf::kEngineWideGroupW : mf::kEngineGroupW; }
+// Columns per lane and per map unit of a path, for maps of map_dtype.
+int path_cpt(int path, int map_dtype) {
+  return path ? mf::engine_wide_cpt((int)dtype_bytes(map_dtype)) : mf::kEngineCPT;
+}
+int path_group_w(int path, int map_dtype) { return 8 * 32 * path_cpt(path, map_dtype); }
 
-// The 16-point, 4-columns-per-lane path serves windows up to 16 points on
-// widths divisible by 4; every other stream takes the 32-point path.
-int stream_path(int width, int window) { return window <= mf::kEngineWideNMAX && width % 4 == 0 ? 1 : 0; }
+// The 16-point path serves windows up to 16 points on widths divisible by
+// its columns per lane; every other stream takes the 32-point path.
+int stream_path(int width, int window, int map_dtype) {
+  return window <= mf::kEngineWideNMAX && width % path_cpt(1, map_dtype) == 0 ? 1 : 0;
+}
 
 }  // namespace
 
@@ -434,7 +439,7 @@ int tune_class(mf_engine* e, int width, int height, int window, int* band_out) {
   std::vector<TickPush> pushes(1);
   pushes[0].slot = e->d.max_streams;
   std::vector<double> no_poses;
-  const int path = stream_path(width, window);
+  const int path = stream_path(width, window, e->d.map_dtype);
   for (int bh : band_candidates(height)) {
     std::vector<TickFrame> frs(frames);
     for (int f = 0; f < frames; ++f) {
@@ -446,7 +451,7 @@ int tune_class(mf_engine* e, int width, int height, int window, int* band_out) {
       t.path = path;
       t.band_h = bh;
       t.bands = (height + bh - 1) / bh;
-      t.groups_x = (width + path_group_w(path) - 1) / path_group_w(path);
+      t.groups_x = (width + path_group_w(path, e->d.map_dtype) - 1) / path_group_w(path, e->d.map_dtype);
       char* base = buf + (size_t)f * per_frame;
       t.depth = base;
       t.M = base + pin * dtype_bytes(e->d.depth_dtype);
@@ -639,10 +644,10 @@ int mf_engine_add_stream(mf_engine* e, const mf_stream_desc* d, int64_t reserve_
   s.reserve = reserve_bytes;
   s.plane_in = (size_t)d->width * d->height * dtype_bytes(d->depth_dtype);
   s.plane_out = (size_t)d->width * d->height * dtype_bytes(d->map_dtype);
-  s.path = stream_path(d->width, std::min(d->window, (int)mf::kMaxPts));
+  s.path = stream_path(d->width, std::min(d->window, (int)mf::kMaxPts), e->d.map_dtype);
   s.band_h = band;
   s.bands = (d->height + band - 1) / band;
-  s.groups_x = (d->width + path_group_w(s.path) - 1) / path_group_w(s.path);
+  s.groups_x = (d->width + path_group_w(s.path, e->d.map_dtype) - 1) / path_group_w(s.path, e->d.map_dtype);
   // stream-ordered upload from pinned staging: earlier ticks never read this
   // slot (it was free), later ticks see it; nothing waits
   fill_slot_params(s, w, e->slots_pinned + free_slot);
@@ -703,17 +708,18 @@ int mf::engine_submit_at(mf_engine* e, int32_t slot, int32_t n, const double* po
       (guided_depth && (uintptr_t)guided_depth % (2 * dtype_bytes(e->d.map_dtype))) ||
       (info && (uintptr_t)info % 8))
     return fail(MF_ERR_INVALID_ARG, "misaligned plane or record pointer");
-  // the wide path reads and writes four elements at a time; a push whose
-  // planes are not aligned to that runs on the 32-point path
+  // the 16-point path reads and writes path_cpt(1) elements at a time; a
+  // push whose planes are not aligned to that runs on the 32-point path
   int path = s.path, band_h = s.band_h, bands = s.bands, groups_x = s.groups_x;
+  const size_t wc = (size_t)path_cpt(1, e->d.map_dtype);
   if (path == 1 &&
-      ((depth && (uintptr_t)depth % (4 * dtype_bytes(e->d.depth_dtype))) ||
-       (focus_map && (uintptr_t)focus_map % (4 * dtype_bytes(e->d.map_dtype))) ||
-       (guided_depth && (uintptr_t)guided_depth % (4 * dtype_bytes(e->d.map_dtype))))) {
+      ((depth && (uintptr_t)depth % (wc * dtype_bytes(e->d.depth_dtype))) ||
+       (focus_map && (uintptr_t)focus_map % (wc * dtype_bytes(e->d.map_dtype))) ||
+       (guided_depth && (uintptr_t)guided_depth % (wc * dtype_bytes(e->d.map_dtype))))) {
     path = 0;
     band_h = default_band(s.d.height);
     bands = (s.d.height + band_h - 1) / band_h;
-    groups_x = (s.d.width + path_group_w(0) - 1) / path_group_w(0);
+    groups_x = (s.d.width + path_group_w(0, e->d.map_dtype) - 1) / path_group_w(0, e->d.map_dtype);
   }
   TickPush ps{};
   ps.slot = slot;

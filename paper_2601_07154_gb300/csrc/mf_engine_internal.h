@@ -8,14 +8,15 @@
 namespace mf {
 
 // Two map paths: every stream can take the 32-point path with 2 columns per
-// lane; streams with windows up to 16 points and widths divisible by 4 take
-// the 16-point path with 4 columns per lane (fewer instructions per pixel).
+// lane; streams with windows up to 16 points and widths divisible by the
+// 16-point path's columns per lane take that path (16-bit maps: 4 columns
+// per lane, fewer instructions per pixel; FP32 maps: 2, whose smaller unit
+// fits three CTAs per SM).
 constexpr int kEngineCPT = 2;                           // columns per lane, 32-point path
 constexpr int kEngineGroupW = 8 * 32 * kEngineCPT;      // columns per map unit
 constexpr int kEngineWideNMAX = 16;
-constexpr int kEngineWideCPT = 4;
-constexpr int kEngineWideGroupW = 8 * 32 * kEngineWideCPT;
-constexpr int kEnginePaths = 2;                         // 0: 32-point, 1: 16-point wide
+__host__ __device__ constexpr int engine_wide_cpt(int map_bytes) { return map_bytes == 4 ? 2 : 4; }
+constexpr int kEnginePaths = 2;                         // 0: 32-point, 1: 16-point
 
 // Per admitted stream, written once at admission (device array by slot).
 struct SlotParams {

@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(kEngPtsWarps * 32) engine_points_kernel(Engine
 // frames.  Each path is its own kernel: one kernel holding both the 16- and
 // the 32-point unit would not fit the register budget.
 template <typename TIn, typename TOut, int NMAX, int CPT, int PATH>
-__global__ void __launch_bounds__(kMapThreads, 2) engine_map_kernel(EngineKernelArgs a) {
+__global__ void __launch_bounds__(kMapThreads, unit_ctas_per_sm(NMAX, CPT)) engine_map_kernel(EngineKernelArgs a) {
   extern __shared__ float4 smem4[];
   __shared__ PointsSmem<kMaxPts> P;
   __shared__ int s_kept;
@@ -120,7 +120,7 @@ namespace {
 template <typename TIn, typename TOut, int PATH>
 struct MapKernel {
   static constexpr int kN = PATH ? kEngineWideNMAX : kMaxPts;
-  static constexpr int kC = PATH ? kEngineWideCPT : kEngineCPT;
+  static constexpr int kC = PATH ? engine_wide_cpt((int)sizeof(TOut)) : kEngineCPT;
   static size_t smem() { return unit_smem_bytes(kN, kBandMax, kC, (int)sizeof(TIn)); }
   static int grid() {
     static int g = 0;

@@ -254,7 +254,8 @@ __global__ void __launch_bounds__(kMapThreads) map_kernel(MapParams p) {
 // up to 256 rows x group of 8 strips) in frame order from the dynamic
 // schedule; map_unit does the work.
 template <int NMAX, int CPT, typename TIn, typename TOut, int MODE>
-__global__ void __launch_bounds__(kMapThreads, 2) map_stream_kernel(MapParams p, int band_h) {
+__global__ void __launch_bounds__(kMapThreads, unit_ctas_per_sm(NMAX, CPT))
+    map_stream_kernel(MapParams p, int band_h) {
   extern __shared__ float4 smem4[];
   float* Ey = reinterpret_cast<float*>(smem4);                          // [band_h][NMAX]
   uint4* ring = reinterpret_cast<uint4*>(Ey + (size_t)band_h * NMAX);   // [8][stages][32]
@@ -409,8 +410,12 @@ cudaError_t launch_typed(const MapParams& p, bool norm_max, cudaStream_t st, int
   const long long tiles = (long long)p.n_frames * p.tiles_x * p.tiles_y;
   if (tiles <= 0) return cudaSuccess;
   if (tiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  // windows up to 16 points: 4 columns per lane; 32 points: 2 (register budget)
-  constexpr int CPT = NMAX <= 16 ? 4 : 2;
+  // Pixels per lane.  FP32 maps: 2, so that windows of up to 16 points fit
+  // three CTAs (24 warps) per SM, whose extra loads in flight beat the wider
+  // rows (1080p ACCEL, window 16: 1.20 vs 1.16 of measured HBM).  16-bit maps
+  // keep 4 (8-byte stores; 2 pixels lose 20 %), and 32 points need 2 for the
+  // register budget.
+  constexpr int CPT = (NMAX > 16 || sizeof(TOut) == 4) ? 2 : 4;
   auto aligned = [](const void* q, size_t a) { return q == nullptr || ((uintptr_t)q % a) == 0; };
   const bool vec = (p.width % CPT) == 0 && aligned(p.depth, CPT * sizeof(TIn)) &&
                    aligned(p.M, CPT * sizeof(TOut)) && aligned(p.G, CPT * sizeof(TOut));

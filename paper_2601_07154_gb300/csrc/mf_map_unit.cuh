@@ -531,6 +531,11 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
   if (MODE != kUnitScaled && lane == 0 && n > 0 && key) atomicMax(&rec->argmax_key, key);
 }
 
+// Resident CTAs per SM the persistent map kernels are compiled for: three
+// where 2 pixels per lane and at most 16 points keep the unit within 85
+// registers, else two (the 128-register unit).
+__host__ __device__ constexpr int unit_ctas_per_sm(int nmax, int cpt) { return cpt == 2 && nmax <= 16 ? 3 : 2; }
+
 // Dynamic shared memory of a CTA running units of bucket NMAX with CPT
 // pixels per lane and in_bytes-byte depth: the band's row factors, then
 // every warp's depth ring.

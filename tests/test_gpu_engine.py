@@ -59,12 +59,13 @@ def _inputs(spec):
     return poses, depth, K
 
 
-def _run_engine(mf, specs, chunk=7, graph=True, tune=True, only=None, offset=0):
+def _run_engine(mf, specs, chunk=7, graph=True, tune=True, only=None, offset=0, dtype=torch.float32):
     """Feed each stream in chunks, one push per stream per tick; returns per-stream outputs.
-    `offset` shifts every plane buffer by that many elements (alignment tests)."""
+    `offset` shifts every plane buffer by that many elements (alignment tests);
+    `dtype` is the depth and map storage type."""
     dev = torch.device("cuda", 0)
     eng = mf.MotionFocusEngine(max_streams=8, max_tick_frames=512, max_stream_frames=16,
-                               graph=graph, tune=tune, device=dev)
+                               depth_dtype=dtype, map_dtype=dtype, graph=graph, tune=tune, device=dev)
     state = []
     for idx, spec in enumerate(specs):
         if only is not None and idx not in only:
@@ -76,9 +77,9 @@ def _run_engine(mf, specs, chunk=7, graph=True, tune=True, only=None, offset=0):
 
         def planes(data=None):
             n = frames * height * width
-            buf = torch.zeros(n + offset, device=dev)
+            buf = torch.zeros(n + offset, dtype=dtype, device=dev)
             if data is not None:
-                buf[offset:] = torch.from_numpy(data).reshape(-1).to(dev)
+                buf[offset:] = torch.from_numpy(data).reshape(-1).to(dev).to(dtype)
             return buf[offset:].view(frames, height, width)
 
         M, G = planes(), planes()
@@ -103,7 +104,7 @@ def _run_engine(mf, specs, chunk=7, graph=True, tune=True, only=None, offset=0):
         if s is None:
             out.append(None)
             continue
-        out.append((s["M"].cpu().numpy(), s["G"].cpu().numpy(),
+        out.append((s["M"].float().cpu().numpy(), s["G"].float().cpu().numpy(),
                     s["info"].cpu().numpy().view(mf.FRAME_INFO_DTYPE)))
     eng.close()
     return out, stats
@@ -129,23 +130,26 @@ def test_engine_mixed_streams_match_oracle(mf):
         assert info["n_valid"].sum() > 0
 
 
-def test_engine_planes_aligned_to_two_elements_take_the_32_point_path(mf):
-    """Planes shifted by two FP32 elements (8-byte aligned) cannot take the
-    4-pixels-per-lane path: the engine renders those pushes on the 32-point
-    path, within the oracle tolerance, and no wide-path fault or misread."""
-    specs = [STREAMS[0], STREAMS[4]]      # both wide-path streams when aligned
-    outs, _ = _run_engine(mf, specs, offset=2)
-    ref_outs, _ = _run_engine(mf, specs)
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_engine_planes_aligned_to_two_elements(mf, storage):
+    """Planes shifted by two elements.  FP32 maps stay on the 16-point path
+    (2 pixels per lane: 8-byte accesses); 16-bit maps cannot take its
+    4-pixel accesses, and the engine renders those pushes on the 32-point
+    path.  Either way the maps match the oracle, with no fault or misread."""
+    dt = {"f32": torch.float32, "bf16": torch.bfloat16}[storage]
+    specs = [STREAMS[0], STREAMS[4]]      # both 16-point-path streams when aligned
+    outs, _ = _run_engine(mf, specs, offset=2, dtype=dt)
+    ref_outs, _ = _run_engine(mf, specs, dtype=dt)
     for spec, (M, G, info), (Ma, Ga, infoa) in zip(specs, outs, ref_outs):
         width, height, window, smooth_len, mode, seed, frames = spec
         poses, depth, K = _inputs(spec)
         ref = O.OracleStream(O.Params(width, height, window=window, smooth_len=smooth_len,
                                       mode=O.MODE_ACCEL if mode == "accel" else O.MODE_HEADING))
-        ref.push(poses, depth.astype(np.float64), K)
+        ref.push(poses, torch.from_numpy(depth).to(dt).double().numpy(), K)
         for n in range(frames):
             _, _, Mr, Gr = ref.frame(n)
-            parity.check_map(M[n], Mr, where=f"{spec} M {n}")
-            parity.check_map(G[n], Gr, where=f"{spec} G {n}")
+            parity.check_map(M[n], Mr, storage, where=f"{spec} M {n}")
+            parity.check_map(G[n], Gr, storage, where=f"{spec} G {n}")
         for k in parity.INT_FIELDS:
             assert np.array_equal(info[k], infoa[k]), k
 
