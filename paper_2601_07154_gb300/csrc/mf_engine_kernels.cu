@@ -70,7 +70,9 @@ __global__ void __launch_bounds__(kMapThreads, unit_ctas_per_sm(NMAX, CPT)) engi
   const TickPush* pushes = tick_pushes(tab);
   float* Ey = reinterpret_cast<float*>(smem4);
   uint4* ring = reinterpret_cast<uint4*>(Ey + (size_t)kBandMax * NMAX);
-  uint4* my_ring = ring + (size_t)(threadIdx.x >> 5) * ring_stages(CPT, (int)sizeof(TIn)) * 32;
+  // this warp's ring: S rows of 32 lanes x CPT depth elements (uint4 units)
+  uint4* my_ring = ring + (size_t)(threadIdx.x >> 5) * ring_stages(CPT, (int)sizeof(TIn), NMAX) * 2 * CPT *
+                             (int)sizeof(TIn);
   __shared__ long long s_next[2];
   long long u = blockIdx.x;
   for (int k = 0; u < units; ++k) {

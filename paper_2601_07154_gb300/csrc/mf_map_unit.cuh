@@ -35,10 +35,37 @@ namespace mf {
 
 constexpr float kCullBelow = 9.094947017729282e-13f;  // 2^-40
 
-// Depth rows in flight per warp: kStages rows of 16 bytes per lane, and
-// proportionally more rows where a lane reads fewer bytes per row (2 pixels,
-// or 16-bit depth), so every ring holds the same bytes in flight.
-__host__ __device__ constexpr int ring_stages(int cpt, int in_bytes) { return kStages * 16 / (cpt * in_bytes); }
+// Resident CTAs per SM the persistent map kernels are compiled for: three
+// where 2 pixels per lane and at most 16 points keep the unit within 85
+// registers, else two (the 128-register unit).
+__host__ __device__ constexpr int unit_ctas_per_sm(int nmax, int cpt) { return cpt == 2 && nmax <= 16 ? 3 : 2; }
+
+// Depth rows in flight per warp; the ring packs a row at CPT x in_bytes
+// bytes per lane.  Rows of 16 bytes per lane: kStages.  Narrower rows: 2 KB
+// per warp where three CTAs share an SM, 4 KB where two do (1080p frames:
+// the 4 KB ring gains 2-6 % with two CTAs per SM and loses about 1 % with
+// three).
+__host__ __device__ constexpr int ring_stages(int cpt, int in_bytes, int nmax) {
+  return cpt * in_bytes >= 16 ? kStages
+                              : (unit_ctas_per_sm(nmax, cpt) == 3 ? 2048 : 4096) / (32 * cpt * in_bytes);
+}
+
+// A lane's depth bytes of ring row slot `slot` (rows packed at BYTES per lane).
+template <int BYTES>
+__device__ __forceinline__ uint4 ring_row(const uint4* ring, int slot) {
+  const char* q = reinterpret_cast<const char*>(ring) + slot * BYTES;
+  uint4 v = make_uint4(0u, 0u, 0u, 0u);
+  if (BYTES == 16) {
+    v = *reinterpret_cast<const uint4*>(q);
+  } else if (BYTES == 8) {
+    const uint2 t = *reinterpret_cast<const uint2*>(q);
+    v.x = t.x;
+    v.y = t.y;
+  } else {
+    v.x = *reinterpret_cast<const unsigned*>(q);
+  }
+  return v;
+}
 
 template <int NMAX>
 struct PointsSmem {
@@ -251,7 +278,7 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
                                          PointsSmem<kMaxPts>& P, int& s_kept, const uint4* zeros) {
   constexpr int kInBytes = CPT * (int)sizeof(TIn);
   constexpr int kStrip = 32 * CPT;
-  constexpr int S = ring_stages(CPT, (int)sizeof(TIn));
+  constexpr int S = ring_stages(CPT, (int)sizeof(TIn), NMAX);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int rows = ug.rows, y0 = ug.y0;
   const int x0 = ug.gx0 + warp * kStrip;
@@ -264,7 +291,8 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
   static_assert((S & (S - 1)) == 0, "ring stages must be a power of two");
   auto issue = [&](int r) {
     if (r < rows && col_ok && dsrc)
-      cp_async<kInBytes>(my_ring + (r & (S - 1)) * 32 + lane, dsrc + (size_t)r * dstride);
+      cp_async<kInBytes>(reinterpret_cast<char*>(my_ring) + ((r & (S - 1)) * 32 + lane) * kInBytes,
+                         dsrc + (size_t)r * dstride);
     cp_async_commit();
   };
   // The ring is this warp's own and the previous unit drained it.
@@ -502,8 +530,8 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
 #pragma unroll
     for (int c = 0; c < CPT; ++c) d0v[c] = d1v[c] = 0.0f;
     if (dsrc) {
-      Vec<TIn, CPT>::unpack(my_ring[(r & (S - 1)) * 32 + lane], d0v);
-      if (two) Vec<TIn, CPT>::unpack(my_ring[((r + 1) & (S - 1)) * 32 + lane], d1v);
+      Vec<TIn, CPT>::unpack(ring_row<kInBytes>(my_ring, (r & (S - 1)) * 32 + lane), d0v);
+      if (two) Vec<TIn, CPT>::unpack(ring_row<kInBytes>(my_ring, ((r + 1) & (S - 1)) * 32 + lane), d1v);
     }
     float2 a[CPT / 2], b[CPT / 2];
 #pragma unroll
@@ -531,16 +559,12 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
   if (MODE != kUnitScaled && lane == 0 && n > 0 && key) atomicMax(&rec->argmax_key, key);
 }
 
-// Resident CTAs per SM the persistent map kernels are compiled for: three
-// where 2 pixels per lane and at most 16 points keep the unit within 85
-// registers, else two (the 128-register unit).
-__host__ __device__ constexpr int unit_ctas_per_sm(int nmax, int cpt) { return cpt == 2 && nmax <= 16 ? 3 : 2; }
-
 // Dynamic shared memory of a CTA running units of bucket NMAX with CPT
 // pixels per lane and in_bytes-byte depth: the band's row factors, then
 // every warp's depth ring.
 __host__ __device__ constexpr size_t unit_smem_bytes(int nmax, int band_h, int cpt, int in_bytes) {
-  return (size_t)band_h * nmax * 4 + (size_t)(kMapThreads / 32) * ring_stages(cpt, in_bytes) * 32 * 16;
+  return (size_t)band_h * nmax * 4 +
+         (size_t)(kMapThreads / 32) * ring_stages(cpt, in_bytes, nmax) * 32 * cpt * in_bytes;
 }
 
 // Dynamic unit schedule of the persistent map kernels.  CTA c starts on
