@@ -250,6 +250,16 @@ __device__ __forceinline__ void accum_two_rows(const float2 (&ex)[NMAX][CPT / 2]
   }
 }
 
+// Warp-wide maximum of the lanes' argmax keys, published to the frame's
+// record by lane 0 (frames without valid points keep key 0).
+__device__ __forceinline__ void publish_key(FrameRec* rec, unsigned long long key, bool any_points) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
+    key = k2 > key ? k2 : key;
+  }
+  if ((threadIdx.x & 31) == 0 && any_points && key) atomicMax(&rec->argmax_key, key);
+}
+
 // One unit of one frame.  planes point at the frame's first pixel; the
 // caller guarantees width % CPT == 0 and CPT-element alignment of all
 // planes.  Every thread of the CTA must call this (it holds barriers).
@@ -301,6 +311,34 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
   FrameRec* rec = ug.rec;
   const int n = rec->n_valid;
   const float inv_n = rec->inv_n;
+  // This warp's strip as zeros: its rows (when write_rows; plain CPT-element
+  // stores, or with bulk one bulk copy per row and map, which needs 16-byte
+  // aligned rows) and its argmax candidate, the strip's first pixel (0).
+  auto zero_strip = [&](bool write_rows, bool bulk) {
+    if (write_rows && MODE != kUnitMaxOnly) {
+      if (bulk) {
+        const uint32_t bytes = (uint32_t)(min(kStrip, ug.width - x0) * (int)sizeof(TOut));
+        const size_t first = (size_t)y0 * ug.width + x0;
+        for (int r = lane; r < rows; r += 32) {
+          const size_t at = (first + (size_t)r * ug.width) * sizeof(TOut);
+          if (ug.M) bulk_copy_s2g(ug.M + at, zeros, bytes);
+          if (ug.G) bulk_copy_s2g(ug.G + at, zeros, bytes);
+        }
+        bulk_commit();
+      } else if (col_ok) {
+        const float z[CPT] = {};
+        const size_t ostride = (size_t)ug.width * sizeof(TOut);
+        char* qm = ug.M ? ug.M + row0 * sizeof(TOut) : nullptr;
+        char* qg = ug.G ? ug.G + row0 * sizeof(TOut) : nullptr;
+        for (size_t off = 0, end = (size_t)rows * ostride; off < end; off += ostride) {
+          if (qm) Vec<TOut, CPT>::store(qm + off, 0, z);
+          if (qg) Vec<TOut, CPT>::store(qg + off, 0, z);
+        }
+      }
+    }
+    if (MODE != kUnitScaled)
+      publish_key(rec, col_ok ? (unsigned long long)(0xffffffffu - (unsigned)(y0 * ug.width + xc)) : 0ull, n > 0);
+  };
   if (warp == 0) {
     bool keep = false;
     float uh = 0.f, ul = 0.f, vh = 0.f, vl = 0.f, ch = 0.f, cl = 0.f;
@@ -355,25 +393,7 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
       bulk_commit();
     }
     if (x0 >= ug.width) return;  // warp-uniform: this strip lies past the frame
-    if (!bulk && MODE != kUnitMaxOnly && col_ok) {
-      const float z[CPT] = {};
-      const size_t ostride = (size_t)ug.width * sizeof(TOut);
-      char* qm = ug.M ? ug.M + row0 * sizeof(TOut) : nullptr;
-      char* qg = ug.G ? ug.G + row0 * sizeof(TOut) : nullptr;
-      for (size_t off = 0, end = (size_t)rows * ostride; off < end; off += ostride) {
-        if (qm) Vec<TOut, CPT>::store(qm + off, 0, z);
-        if (qg) Vec<TOut, CPT>::store(qg + off, 0, z);
-      }
-    }
-    if (MODE != kUnitScaled) {
-      unsigned long long key =
-          col_ok ? (unsigned long long)(0xffffffffu - (unsigned)(y0 * ug.width + xc)) : 0ull;
-      for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
-        key = k2 > key ? k2 : key;
-      }
-      if (lane == 0 && n > 0 && key) atomicMax(&rec->argmax_key, key);
-    }
+    zero_strip(!bulk, false);  // with bulk the CTA's copies above wrote the rows
     return;
   }
   // Depth only scales G: with no G output, or no point kept (M = 0, so G = 0
@@ -412,7 +432,7 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
 #pragma unroll
       for (int c = 0; c < CPT / 2; ++c) {
         float e0 = 0.f, e1 = 0.f;
-        if (i < nk && col_ok) {
+        if (i < nk && col_ok && !strip_zero) {
           e0 = gauss_factor((float)(xc + 2 * c), P.uhi[i], P.ulo[i], P.chi[i], P.clo[i]);
           e1 = gauss_factor((float)(xc + 2 * c + 1), P.uhi[i], P.ulo[i], P.chi[i], P.clo[i]);
         }
@@ -423,36 +443,7 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
   __syncthreads();  // Ey complete
   if (x0 >= ug.width) return;  // warp-uniform: this strip lies past the frame (no copies issued)
   if (strip_zero) {
-    if (MODE != kUnitMaxOnly) {
-      if (bulk) {
-        const uint32_t bytes = (uint32_t)(min(kStrip, ug.width - x0) * (int)sizeof(TOut));
-        const size_t first = (size_t)y0 * ug.width + x0;
-        for (int r = lane; r < rows; r += 32) {
-          const size_t at = (first + (size_t)r * ug.width) * sizeof(TOut);
-          if (ug.M) bulk_copy_s2g(ug.M + at, zeros, bytes);
-          if (ug.G) bulk_copy_s2g(ug.G + at, zeros, bytes);
-        }
-        bulk_commit();
-      } else if (col_ok) {
-        const float z[CPT] = {};
-        const size_t ostride = (size_t)ug.width * sizeof(TOut);
-        char* qm = ug.M ? ug.M + row0 * sizeof(TOut) : nullptr;
-        char* qg = ug.G ? ug.G + row0 * sizeof(TOut) : nullptr;
-        for (size_t off = 0, end = (size_t)rows * ostride; off < end; off += ostride) {
-          if (qm) Vec<TOut, CPT>::store(qm + off, 0, z);
-          if (qg) Vec<TOut, CPT>::store(qg + off, 0, z);
-        }
-      }
-    }
-    if (MODE != kUnitScaled) {
-      unsigned long long key =
-          col_ok ? (unsigned long long)(0xffffffffu - (unsigned)(y0 * ug.width + xc)) : 0ull;
-      for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
-        key = k2 > key ? k2 : key;
-      }
-      if (lane == 0 && n > 0 && key) atomicMax(&rec->argmax_key, key);
-    }
+    zero_strip(true, bulk);
     return;
   }
 
@@ -550,13 +541,9 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
     if (MODE != kUnitScaled) track(a, b, two, r);
   }
   cp_async_wait<0>();
-  unsigned long long key =
-      best >= 0.0f ? ((unsigned long long)__float_as_uint(best) << 32) | (0xffffffffu - bidx) : 0ull;
-  for (int o = 16; o > 0; o >>= 1) {
-    const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
-    key = k2 > key ? k2 : key;
-  }
-  if (MODE != kUnitScaled && lane == 0 && n > 0 && key) atomicMax(&rec->argmax_key, key);
+  if (MODE != kUnitScaled)
+    publish_key(rec, best >= 0.0f ? ((unsigned long long)__float_as_uint(best) << 32) | (0xffffffffu - bidx) : 0ull,
+                n > 0);
 }
 
 // Dynamic shared memory of a CTA running units of bucket NMAX with CPT
