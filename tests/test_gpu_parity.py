@@ -482,6 +482,49 @@ def test_streams_alone_and_interleaved_identical(mf):
     sb.close()
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_streams_rendering_concurrently_identical(mf, kernel):
+    """Two streams whose map launches run at the same time on their own CUDA
+    streams (each stream owns its work counter) render exactly the maps each
+    renders alone."""
+    dev = torch.device("cuda", 0)
+    ws = [hd_stream(seed=s, n_frames=64) for s in (3, 4)]
+    rings = [torch.from_numpy(np.stack([w.depth(k) for k in range(w.ring)])).to(dev) for w in ws]
+    idx = torch.tensor([k % ws[0].ring for k in range(64)], device=dev)
+    depths = [r[idx].contiguous() for r in rings]
+    poses = [torch.from_numpy(w.poses).to(dev) for w in ws]
+    torch.cuda.synchronize(dev)  # inputs are ready before other CUDA streams read them
+
+    def open_stream(cs):
+        return mf.MotionFocusStream(1920, 1080, window=16, smooth_len=15, mode="heading", device=dev,
+                                    cuda_stream=cs, map_kernel=kernel)
+
+    alone = []
+    for w, p, d in zip(ws, poses, depths):
+        s = open_stream(torch.cuda.Stream(dev))
+        s.push(p, d, w.K())
+        alone.append(s.get_maps())
+        s.close()
+    torch.cuda.synchronize(dev)
+    streams = [open_stream(torch.cuda.Stream(dev)) for _ in ws]
+    for s, w, p, d in zip(streams, ws, poses, depths):
+        s.push(p, d, w.K())
+    outs = []
+    for s in streams:  # enqueue both renders before waiting for either
+        M = torch.empty((64, 1080, 1920), device=dev)
+        G = torch.empty_like(M)
+        info = torch.empty(64 * mf._mf.FRAME_INFO_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+        with torch.cuda.device(dev):
+            assert mf._mf.mf_get_maps(s.handle, 64, M, G, info, None) == 64
+        outs.append((M, G, info))
+    for s in streams:
+        s.torch_stream.synchronize()
+        s.close()
+    for a, (M, G, info) in zip(alone, outs):
+        assert torch.equal(a[0], M) and torch.equal(a[1], G)
+        assert np.array_equal(a[2], info.cpu().numpy().view(mf._mf.FRAME_INFO_DTYPE))
+
+
 # ---------------------------------------------------------- full workload --
 @pytest.mark.parametrize("kernel,storage", [("cuda_cores", "f32"), ("tensor_cores", "f32"),
                                             ("tensor_cores", "bf16")])
