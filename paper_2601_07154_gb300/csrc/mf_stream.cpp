@@ -557,7 +557,7 @@ int mf_open_stream(const mf_stream_desc* d, mf_stream** out) {
   s->sched = (unsigned int*)s->dalloc(sizeof(unsigned int));
   if (!s->recs || !s->sched) {
     destroy(s);
-    return fail(MF_ERR_OOM, "frame record allocation failed");
+    return fail(MF_ERR_OOM, "frame record or work counter allocation failed");
   }
   // every map launch of the stream leaves its counter at 0 again
   if (cudaMemsetAsync(s->sched, 0, sizeof(unsigned int), s->st) != cudaSuccess) {
