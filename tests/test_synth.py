@@ -35,3 +35,37 @@ def test_workload_shapes():
     assert all((m.width, m.height) in ((640, 480), (1280, 720), (1920, 1080), (3840, 2160))
                for m in ms)
     assert all(120 <= m.n_frames <= 1800 and 8 <= m.window <= 32 for m in ms)
+
+
+def test_walker_follows_its_recipe():
+    """30 fps walker at 1.4 m/s, 10 deg / 0.5 Hz yaw sway, 3 deg / 2 Hz pitch
+    bob, 1 cm and 0.5 deg pose noise, turns bounded by 45 deg/s."""
+    from synth import WalkerSpec, walk
+    tr = walk(WalkerSpec(n_frames=600, seed=3, turns=True))
+    step = np.linalg.norm(np.diff(tr.body_pos, axis=0), axis=1)
+    assert np.allclose(step, 1.4 / 30.0, rtol=1e-12)
+    rate = np.abs(np.diff(tr.body_yaw)) * 30.0
+    assert rate.max() <= np.radians(45.0) + 1e-12 and rate.max() > np.radians(5.0)
+    noise = tr.centres - tr.body_pos
+    assert abs(noise.std() - 0.01) < 0.002 and abs(noise.mean()) < 0.002
+    # camera yaw about the body heading: sway of 10 deg (+ 0.5 deg noise)
+    fwd = tr.rot_c2w[:, :, 2]
+    yaw = np.arctan2(fwd[:, 0], fwd[:, 2])
+    rel = np.degrees(np.angle(np.exp(1j * (yaw - tr.body_yaw))))
+    assert 9.0 < np.abs(rel).max() < 12.5
+    # world-to-camera poses invert the camera-to-world ones
+    R = tr.poses_w2c[:, :, :3]
+    assert np.allclose(R, np.swapaxes(tr.rot_c2w, 1, 2), atol=1e-12)
+    assert np.allclose(np.einsum("nij,nj->ni", R, tr.centres) + tr.poses_w2c[:, :, 3], 0.0, atol=1e-12)
+
+
+def test_scene_boxes_follow_their_recipe():
+    """20 boxes, footprint 0.3..1.2 m, height 0.5..2.5 m, standing on the ground."""
+    w = hd_stream()
+    boxes = w.boxes
+    assert len(boxes) == 20
+    for b in boxes:
+        size = b.hi - b.lo
+        assert 0.3 <= size[0] <= 1.2 and 0.3 <= size[2] <= 1.2 and 0.5 <= size[1] <= 2.5
+        assert b.hi[1] == 1.6          # the ground plane, 1.6 m below the start (y down)
+    assert w.intr == (1500.0, 1500.0, 960.0, 540.0) and w.window == 16 and w.smooth_len == 15
