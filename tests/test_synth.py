@@ -35,6 +35,11 @@ def test_workload_shapes():
     assert all((m.width, m.height) in ((640, 480), (1280, 720), (1920, 1080), (3840, 2160))
                for m in ms)
     assert all(120 <= m.n_frames <= 1800 and 8 <= m.window <= 32 for m in ms)
+    assert all(0.7 * m.width <= m.intr[0] == m.intr[1] <= 1.2 * m.width for m in ms)
+    assert all(m.intr[2:] == (m.width / 2.0, m.height / 2.0) for m in ms)
+    big = mixed_streams(64)
+    assert {(m.width, m.height) for m in big} == {(640, 480), (1280, 720), (1920, 1080), (3840, 2160)}
+    assert min(m.window for m in big) <= 10 and max(m.window for m in big) >= 30
 
 
 def test_walker_follows_its_recipe():
