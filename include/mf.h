@@ -20,6 +20,8 @@
  *   - Pointers may be host memory (pageable or pinned) or device memory of
  *     the stream's device; the library tells them apart with
  *     cudaPointerGetAttributes.  Managed memory counts as device memory.
+ *     Device memory of another GPU is refused with MF_ERR_INVALID_ARG before
+ *     any work is enqueued (the kernels run on the stream's device only).
  *   - Every entry point returns an mf_status (0 = MF_OK).  No exception or
  *     signal crosses the ABI.  Calls on one mf_stream are not reentrant;
  *     different mf_stream handles may be used from different threads.
@@ -323,6 +325,9 @@ typedef struct {
   int64_t device_bytes;      /* device memory held by the engine */
   int64_t accounted_bytes;   /* engine memory + admitted streams' reservations */
   double tick_gpu_ms;        /* with MF_FLAG_TIME_KERNELS: summed GPU time of the ticks */
+  int64_t frames_path[2];    /* frames rendered by the 32-point map path [0] (any window,
+                                2 columns per lane) and by the 16-point path [1] (windows
+                                up to 16 on widths divisible by its columns per lane) */
 } mf_engine_stats;
 
 /* Defaults: 256 streams, 4096 frames per tick, 64 per stream, FP32, no
@@ -413,6 +418,26 @@ typedef struct {
 
 int mf_engine_latency(mf_engine* e, mf_latency_stats* out, int32_t reset);
 
+/* Latency probe: the engine's completion stamp for work that is not an
+ * engine tick, so that a caller's own per-stream loop (mf_push_frames /
+ * mf_get_maps) is measured on the same clock and by the same mechanism as
+ * the serving loop (the 30 FPS real-time bar of Section 2.2 is a per-frame
+ * latency bound).
+ *   mf_probe_stamp  enqueues on cuda_stream (a cudaStream_t; NULL: the legacy
+ *                   default stream) a host function that records, when every
+ *                   item queued on that stream before it has completed, the
+ *                   latency of n frames: completion time minus each
+ *                   arrival_ns[i] (mf_clock_ns() clock; host array, copied).
+ *   mf_probe_latency  statistics of the stamps completed so far (reset != 0
+ *                   starts a new window).
+ * Stamps are held until read or the probe is closed; mf_probe_close waits
+ * for the stamps still in flight.  A probe is not thread-safe. */
+typedef struct mf_latency_probe mf_latency_probe;
+int mf_probe_open(mf_latency_probe** out);
+int mf_probe_stamp(mf_latency_probe* p, void* cuda_stream, int32_t n, const int64_t* arrival_ns);
+int mf_probe_latency(mf_latency_probe* p, mf_latency_stats* out, int32_t reset);
+int mf_probe_close(mf_latency_probe* p);
+
 /* Wait for all ticks and free everything. */
 int mf_engine_close(mf_engine* e);
 
@@ -488,10 +513,15 @@ int mf_server_close(mf_server* s);
  * GPU loading the library holds until the process exits.  The caller passes and owns the inputs and
  * the outputs.
  *   d              stream descriptor: sizes, window, smooth_len, mode,
- *                  dtypes, sigma/s/d0 parameters and cuda_stream are used;
- *                  pose_frame must be MF_POSES_WORLD; dev_alloc, dev_free,
- *                  max_pending and flags are ignored.  A NULL cuda_stream
- *                  means the legacy default stream.
+ *                  normalize, dtypes, sigma/s/d0 parameters and cuda_stream
+ *                  are used; of the flags, MF_FLAG_MAP_CUDA_CORES and
+ *                  MF_FLAG_MAP_TENSOR_CORES choose the map kernel as for a
+ *                  stream, and the others are ignored; pose_frame must be
+ *                  MF_POSES_WORLD; dev_alloc, dev_free and max_pending are
+ *                  ignored.  A NULL cuda_stream here means the legacy default
+ *                  stream -- unlike mf_open_stream, where NULL asks for a
+ *                  library-owned stream, which this entry point would have to
+ *                  create.
  *   poses_w2c_3x4  n_poses x 12 FP64 world-to-camera poses (device memory)
  *   depth          n_render depth planes of depth_dtype for frames
  *                  n_poses-n_render .. n_poses-1 (device memory) or NULL
@@ -500,8 +530,8 @@ int mf_server_close(mf_server* s);
  *                  n_render planes of map_dtype (device memory) or NULL
  *   info           n_render mf_frame_info records (device memory) or NULL
  * Limits: n_render <= MF_NOALLOC_MAX_FRAMES, n_poses <= MF_NOALLOC_MAX_POSES;
- * larger sizes, host pointers or batch-local poses return
- * MF_ERR_INVALID_ARG before any work is enqueued.  The call only enqueues
+ * larger sizes, host pointers, pointers to another GPU's memory or
+ * batch-local poses return MF_ERR_INVALID_ARG before any work is enqueued.  The call only enqueues
  * kernels on cuda_stream; results are ready when that stream reaches them.
  * It calls no cudaMalloc, cudaFree or other allocating routine.
  * The first call on a device looks up the scratch array's device address

@@ -35,7 +35,8 @@ EXPORTED = ("mf_stream_desc_init", "mf_open_stream", "mf_push_frames", "mf_get_m
             "mf_server_desc_init", "mf_server_open", "mf_server_add_stream", "mf_server_submit",
             "mf_server_frames_done", "mf_server_remove_stream", "mf_server_drain",
             "mf_server_latency", "mf_server_get_stats", "mf_server_close", "mf_clock_ns",
-            "mf_engine_submit_batch", "mf_server_submit_batch", "mf_server_tune")
+            "mf_engine_submit_batch", "mf_server_submit_batch", "mf_server_tune",
+            "mf_probe_open", "mf_probe_stamp", "mf_probe_latency", "mf_probe_close")
 MF_ENGINE_NO_GRAPH = 2
 MF_ENGINE_NO_TUNE = 4
 MF_NOALLOC_MAX_FRAMES = 256
@@ -86,7 +87,7 @@ class MFEngineStats(ctypes.Structure):
         ("kernel_launches", ctypes.c_int64), ("graph_launches", ctypes.c_int64),
         ("streams", ctypes.c_int32), ("reserved", ctypes.c_int32),
         ("device_bytes", ctypes.c_int64), ("accounted_bytes", ctypes.c_int64),
-        ("tick_gpu_ms", ctypes.c_double),
+        ("tick_gpu_ms", ctypes.c_double), ("frames_path", ctypes.c_int64 * 2),
     ]
 
 
@@ -179,6 +180,10 @@ def _load():
     lib.mf_engine_submit_batch.argtypes = [vp, i32, vp, ctypes.POINTER(i32)]
     lib.mf_server_submit_batch.argtypes = [vp, i32, vp, ctypes.POINTER(i32)]
     lib.mf_server_tune.argtypes = [vp, i32, i32, i32, ctypes.POINTER(i32)]
+    lib.mf_probe_open.argtypes = [ctypes.POINTER(vp)]
+    lib.mf_probe_stamp.argtypes = [vp, vp, i32, vp]
+    lib.mf_probe_latency.argtypes = [vp, ctypes.POINTER(MFLatencyStats), i32]
+    lib.mf_probe_close.argtypes = [vp]
     for name in ("mf_open_stream", "mf_push_frames", "mf_get_maps", "mf_sync",
                  "mf_pending_frames", "mf_reset_stream", "mf_stream_stats", "mf_close_stream",
                  "mf_render_noalloc", "mf_engine_open", "mf_engine_add_stream",
@@ -188,7 +193,8 @@ def _load():
                  "mf_server_add_stream", "mf_server_submit", "mf_server_frames_done",
                  "mf_server_remove_stream", "mf_server_drain", "mf_server_latency",
                  "mf_server_get_stats", "mf_server_close", "mf_engine_submit_batch",
-                 "mf_server_submit_batch", "mf_server_tune"):
+                 "mf_server_submit_batch", "mf_server_tune", "mf_probe_open", "mf_probe_stamp",
+                 "mf_probe_latency", "mf_probe_close"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -453,3 +459,27 @@ def mf_server_tune(s, width, height, window):
     _check(lib.mf_server_tune(s, int(width), int(height), int(window), ctypes.byref(b)),
            "mf_server_tune")
     return b.value
+
+
+# ------------------------------------------------------------ latency probe --
+def mf_probe_open():
+    h = ctypes.c_void_p()
+    _check(lib.mf_probe_open(ctypes.byref(h)), "mf_probe_open")
+    return h.value
+
+
+def mf_probe_stamp(p, cuda_stream, arrival_ns):
+    """arrival_ns: int64 numpy array (mf_clock_ns clock); cuda_stream: handle or None."""
+    a = np.ascontiguousarray(arrival_ns, dtype=np.int64)
+    _check(lib.mf_probe_stamp(p, cuda_stream, len(a), a.ctypes.data if len(a) else None),
+           "mf_probe_stamp")
+
+
+def mf_probe_latency(p, reset=False):
+    st = MFLatencyStats()
+    _check(lib.mf_probe_latency(p, ctypes.byref(st), 1 if reset else 0), "mf_probe_latency")
+    return st
+
+
+def mf_probe_close(p):
+    _check(lib.mf_probe_close(p), "mf_probe_close")

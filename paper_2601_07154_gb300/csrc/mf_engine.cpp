@@ -43,15 +43,6 @@ int fail(int st, const char* what, cudaError_t e = cudaSuccess) { return mf::hos
     if (e_ != cudaSuccess) return fail(MF_ERR_CUDA, what, e_); \
   } while (0)
 
-bool on_device(const void* p) {
-  if (!p) return false;
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
 
 struct DeviceGuard {
   int prev = -1;
@@ -71,6 +62,26 @@ int default_band(int height) {
 }
 
 }  // namespace
+
+void mf::latency_summary(const std::vector<double>& v, mf_latency_stats* out) {
+  std::memset(out, 0, sizeof(*out));
+  out->frames = (int64_t)v.size();
+  if (v.empty()) return;
+  std::vector<double> s(v);
+  std::sort(s.begin(), s.end());
+  // nearest-rank percentile: the smallest value with at least p of the samples at or below it
+  auto q = [&](double p) {
+    const size_t i = std::min(s.size() - 1, (size_t)std::ceil(p * s.size()) - (p > 0 ? 1 : 0));
+    return s[i];
+  };
+  out->p50_ms = q(0.50);
+  out->p90_ms = q(0.90);
+  out->p99_ms = q(0.99);
+  out->max_ms = s.back();
+  double sum = 0.0;
+  for (double x : s) sum += x;
+  out->mean_ms = sum / s.size();
+}
 
 int64_t mf::engine_now_ns() {
   return std::chrono::duration_cast<std::chrono::nanoseconds>(
@@ -158,6 +169,7 @@ struct mf_engine {
   std::map<std::tuple<int, int, int>, int> tuned;  // (width, height, window bucket) -> band_h
   // statistics
   int64_t ticks = 0, frames_done = 0, units_done = 0, launches = 0, graph_launches = 0;
+  int64_t frames_path_done[mf::kEnginePaths] = {};
   int64_t device_bytes = 0;
   double tick_ms = 0.0;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending_timers;
@@ -699,9 +711,11 @@ int mf::engine_submit_at(mf_engine* e, int32_t slot, int32_t n, const double* po
     if (!std::isfinite(K[k])) return fail(MF_ERR_INVALID_ARG, "non-finite intrinsics");
   if (!(K[0] > 0.0) || !(K[1] > 0.0)) return fail(MF_ERR_INVALID_ARG, "fx, fy must be > 0");
   DeviceGuard guard(e->device);
-  if (on_device(poses)) return fail(MF_ERR_INVALID_ARG, "engine poses must be host memory");
+  if (mf::host_pointer_kind(poses, e->device) != mf::kPtrHost)
+    return fail(MF_ERR_INVALID_ARG, "engine poses must be host memory");
   for (const void* p : {depth, (const void*)focus_map, (const void*)guided_depth, (const void*)info})
-    if (p && !on_device(p)) return fail(MF_ERR_INVALID_ARG, "engine planes and records must be device memory");
+    if (p && mf::host_pointer_kind(p, e->device) != mf::kPtrDevice)
+      return fail(MF_ERR_INVALID_ARG, "engine planes and records must be device memory of the engine's GPU");
   // two pixels per lane access: planes aligned to two elements
   if ((depth && (uintptr_t)depth % (2 * dtype_bytes(e->d.depth_dtype))) ||
       (focus_map && (uintptr_t)focus_map % (2 * dtype_bytes(e->d.map_dtype))) ||
@@ -823,6 +837,7 @@ int mf_engine_tick(mf_engine* e, int64_t* tick) {
   e->buf_tick[b] = t;
   ++e->ticks;
   e->frames_done += (int64_t)e->frames.size();
+  for (const TickFrame& f : e->frames) ++e->frames_path_done[f.path];
   e->units_done += units;
   e->frames.clear();
   e->pushes.clear();
@@ -881,31 +896,15 @@ int mf_engine_get_stats(mf_engine* e, mf_engine_stats* out) {
   out->device_bytes = e->device_bytes;
   out->accounted_bytes = e->accounted();
   out->tick_gpu_ms = e->tick_ms;
+  for (int p = 0; p < mf::kEnginePaths; ++p) out->frames_path[p] = e->frames_path_done[p];
   return MF_OK;
 }
 
 int mf_engine_latency(mf_engine* e, mf_latency_stats* out, int32_t reset) {
   if (!e || !out) return fail(MF_ERR_INVALID_ARG, "NULL argument");
   collect_latencies(e);
-  std::memset(out, 0, sizeof(*out));
-  std::vector<double>& v = e->latencies_ms;
-  out->frames = (int64_t)v.size();
-  if (!v.empty()) {
-    std::vector<double> s(v);
-    std::sort(s.begin(), s.end());
-    auto q = [&](double p) {
-      const size_t i = std::min(s.size() - 1, (size_t)std::ceil(p * s.size()) - (p > 0 ? 1 : 0));
-      return s[i];
-    };
-    out->p50_ms = q(0.50);
-    out->p90_ms = q(0.90);
-    out->p99_ms = q(0.99);
-    out->max_ms = s.back();
-    double sum = 0.0;
-    for (double x : s) sum += x;
-    out->mean_ms = sum / s.size();
-  }
-  if (reset) v.clear();
+  mf::latency_summary(e->latencies_ms, out);
+  if (reset) e->latencies_ms.clear();
   return MF_OK;
 }
 

@@ -2,6 +2,8 @@
 // kernels (mf_engine_kernels.cu).  Not part of the public ABI.
 #pragma once
 
+#include <vector>
+
 #include "mf_internal.h"
 #include "mf_pose_device.cuh"
 
@@ -106,5 +108,7 @@ int engine_submit_at(mf_engine* e, int32_t slot, int32_t n, const double* poses,
                      const double* K, void* focus_map, void* guided_depth, mf_frame_info* info,
                      int64_t submit_ns);
 int64_t engine_now_ns();
+// p50 / p90 / p99 / max / mean (nearest rank) of latencies in milliseconds.
+void latency_summary(const std::vector<double>& latencies_ms, mf_latency_stats* out);
 
 }  // namespace mf

@@ -124,18 +124,12 @@ struct MapKernel {
   static constexpr int kN = PATH ? kEngineWideNMAX : kMaxPts;
   static constexpr int kC = PATH ? engine_wide_cpt((int)sizeof(TOut)) : kEngineCPT;
   static size_t smem() { return unit_smem_bytes(kN, kBandMax, kC, (int)sizeof(TIn)); }
+  // resident CTAs on the current device (shared memory limit raised there)
   static int grid() {
-    static int g = 0;
-    if (!g) {
-      auto k = engine_map_kernel<TIn, TOut, kN, kC, PATH>;
-      int dev = 0, sms = 0, per = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem());
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, kMapThreads, smem());
-      g = sms * std::max(per, 1);
-    }
-    return g;
+    const KernelFit f = host_kernel_fit(
+        reinterpret_cast<const void*>(engine_map_kernel<TIn, TOut, kN, kC, PATH>), kMapThreads, smem(),
+        smem());
+    return f.sms * f.per_sm;
   }
   static void launch(const EngineKernelArgs& a, int grid, cudaStream_t st) {
     engine_map_kernel<TIn, TOut, kN, kC, PATH><<<grid, kMapThreads, smem(), st>>>(a);

@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include "../../include/mf.h"
+#include "mf_ptr_kind.h"
 
 namespace mf {
 
@@ -150,5 +151,31 @@ int host_validate_desc(const mf_stream_desc* d);
 int host_map_path(uint32_t flags);
 int host_fail(int status, const char* what, cudaError_t e);
 void host_count_launches(int64_t n);
+// Where a caller's pointer lives, for work launched on device `dev`
+// (kPtrHost, kPtrDevice or kPtrOtherDevice of mf_ptr_kind.h).
+int host_pointer_kind(const void* p, int dev);
+// Launch facts of a kernel on the current device: its SM count and the CTAs
+// of `threads` threads with `smem_launch` bytes of dynamic shared memory that
+// fit on one SM.  On first use per (kernel, limit, launch size, device) --
+// with that device current -- the kernel's dynamic shared memory limit is
+// raised to `smem_limit` (and its carveout set when carveout >= 0) on that
+// device; the result is cached under a lock.
+struct KernelFit {
+  int sms = 1;
+  int per_sm = 1;
+};
+KernelFit host_kernel_fit(const void* kernel, int threads, size_t smem_limit, size_t smem_launch,
+                          int carveout = -1);
+
+// Host-side fault injection (mf_fault.cpp; MF_FAULT or mf_set_fault).
+// fault_fires(kind) counts one occurrence of the guarded event and returns
+// true when the installed rule makes this occurrence fail.
+constexpr int kFaultAllocFail = 0;     // a library device allocation returns NULL
+constexpr int kFaultBadPose = 1;       // a host pose is made non-rigid before upload
+constexpr int kFaultDropPush = 2;      // a serving push is accepted, then dropped
+constexpr int kFaultAdmissionFull = 3; // an engine admission is refused
+constexpr int kFaultWaitTimeout = 4;   // a stream wait reports a device wait that ran out
+constexpr int kFaultKinds = 5;
+bool fault_fires(int kind);
 
 }  // namespace mf

@@ -368,17 +368,6 @@ int map_tile_h(int width, int height, int window) {
 
 namespace {
 
-// Resident CTAs per SM and SM count for a kernel (cached per instantiation).
-template <typename K>
-void occupancy(K k, size_t smem_max, int* per_sm, int* sms) {
-  int dev = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k, kMapThreads, smem_max);
-  if (*per_sm < 1) *per_sm = 1;
-}
-
 template <typename T>
 constexpr int out_dtype_of() {
   return std::is_same<T, float>::value ? MF_F32 : std::is_same<T, __half>::value ? MF_F16 : MF_BF16;
@@ -396,12 +385,13 @@ NormalizeParams normalize_params(const MapParams& p) {
   return np;
 }
 
-// Launches the persistent kernel k over `units` units.
+// Launches the persistent kernel k over `units` units: one CTA per unit up
+// to the CTAs the device holds at the band's largest shared memory.
 template <typename K>
-void launch_persistent(K k, int* per_sm, int* sms, size_t smem_max, long long units, size_t smem,
-                       const MapParams& p, int band_h, cudaStream_t st) {
-  if (*per_sm < 0) occupancy(k, smem_max, per_sm, sms);
-  const long long grid = std::min<long long>(units, (long long)*sms * *per_sm);
+void launch_persistent(K k, size_t smem_max, long long units, size_t smem, const MapParams& p,
+                       int band_h, cudaStream_t st) {
+  const KernelFit f = host_kernel_fit(reinterpret_cast<const void*>(k), kMapThreads, smem_max, smem_max);
+  const long long grid = std::min<long long>(units, (long long)f.sms * f.per_sm);
   k<<<(unsigned)grid, kMapThreads, smem, st>>>(p, band_h);
 }
 
@@ -435,23 +425,22 @@ cudaError_t launch_typed(const MapParams& p, bool norm_max, cudaStream_t st, int
         (long long)p.n_frames * bands * ((p.width + kGroupW - 1) / kGroupW);
     const size_t smem_max = unit_smem_bytes(NMAX, kBand, CPT, (int)sizeof(TIn)),
                  smem = unit_smem_bytes(NMAX, band_h, CPT, (int)sizeof(TIn));
-    static int per_sm[3] = {-1, -1, -1}, sms = 0;
     if (!norm_max) {
-      launch_persistent(map_stream_kernel<NMAX, CPT, TIn, TOut, kUnitFull>, &per_sm[0], &sms,
-                        smem_max, units, smem, p, band_h, st);
+      launch_persistent(map_stream_kernel<NMAX, CPT, TIn, TOut, kUnitFull>, smem_max, units, smem, p,
+                        band_h, st);
       *nl += 1;
     } else {
       // same units, same sums: the first pass only finds each frame's maximum
-      launch_persistent(map_stream_kernel<NMAX, CPT, float, float, kUnitMaxOnly>, &per_sm[1], &sms,
-                        smem_max, units, smem, p, band_h, st);
-      launch_persistent(map_stream_kernel<NMAX, CPT, TIn, TOut, kUnitScaled>, &per_sm[2], &sms,
-                        smem_max, units, smem, p, band_h, st);
+      launch_persistent(map_stream_kernel<NMAX, CPT, float, float, kUnitMaxOnly>, smem_max, units, smem,
+                        p, band_h, st);
+      launch_persistent(map_stream_kernel<NMAX, CPT, TIn, TOut, kUnitScaled>, smem_max, units, smem, p,
+                        band_h, st);
       *nl += 2;
     }
   } else {
     const size_t smem = (size_t)NMAX * kTileW * 4 + (size_t)p.tile_h * NMAX * 4;
     auto k = map_kernel<NMAX, TIn, TOut, false>;
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (smem > 48 * 1024) host_kernel_fit(reinterpret_cast<const void*>(k), kMapThreads, smem, smem);
     k<<<(unsigned)tiles, kMapThreads, smem, st>>>(p);
     *nl += 1;
     if (norm_max) {

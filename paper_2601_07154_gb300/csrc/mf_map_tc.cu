@@ -418,32 +418,16 @@ template <typename TIn, typename TOut, bool VEC>
 cudaError_t launch_tc_typed(const MapParams& p, int kk_max, cudaStream_t st) {
   auto k = map_tc_kernel<TIn, TOut, VEC>;
   const size_t smem = tc_smem_bytes(kk_max, sizeof(TIn));
-  static int per_sm[4] = {-1, -1, -1, -1};  // by K' bucket
-  static int sms = 0;
-  const int slot = kk_max / 16 - 1 > 3 ? 3 : kk_max / 16 - 1;
-  if (per_sm[slot] < 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)tc_smem_bytes(kTcKsMax, sizeof(TIn)));
-    cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    // resident CTAs per SM from the kernel's own footprint (shared memory
-    // incl. the per-block reservation, registers), at most 4 for TMEM
-    int smem_sm = 0, reserved = 0, regs_sm = 0;
-    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
-    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
-    cudaFuncAttributes fa{};
-    cudaFuncGetAttributes(&fa, k);
-    const size_t per_cta = smem + fa.sharedSizeBytes + (size_t)reserved;
-    int fit = (int)((size_t)smem_sm / per_cta);
-    if (fa.numRegs > 0) fit = std::min(fit, regs_sm / (fa.numRegs * kTcThreads));
-    per_sm[slot] = std::max(1, std::min(fit, 4));
-  }
+  // resident CTAs per SM from the kernel's footprint (shared memory incl.
+  // the per-block reservation, registers) on this device, at most 4: each
+  // CTA holds 128 TMEM columns, and four fill an SM's 512
+  const KernelFit f = host_kernel_fit(reinterpret_cast<const void*>(k), kTcThreads,
+                                      tc_smem_bytes(kTcKsMax, sizeof(TIn)), smem, 100);
+  const int per_sm = std::max(1, std::min(f.per_sm, 4));
+  const int sms = f.sms;
   const int strips = (p.width + kTcCols - 1) / kTcCols;
   const long long items = (long long)p.n_frames * strips;
-  const long long grid = std::min<long long>(items, (long long)per_sm[slot] * sms);
+  const long long grid = std::min<long long>(items, (long long)per_sm * sms);
   if (items > 0x7fffffffLL) return cudaErrorInvalidConfiguration;  // item indices are int
   k<<<(unsigned)grid, kTcThreads, smem, st>>>(p, strips, kk_max);
   return cudaGetLastError();

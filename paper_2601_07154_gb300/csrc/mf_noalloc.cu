@@ -58,15 +58,6 @@ int scratch_on_current_device(unsigned char** out) {
   return MF_OK;
 }
 
-bool on_device(const void* p) {
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
 }  // namespace
 
 extern "C" int mf_render_noalloc(const mf_stream_desc* d, int32_t n_poses,
@@ -91,10 +82,17 @@ extern "C" int mf_render_noalloc(const mf_stream_desc* d, int32_t n_poses,
     if (!(K[k] == K[k]) || K[k] - K[k] != 0.0)
       return mf::host_fail(MF_ERR_INVALID_ARG, "non-finite intrinsics", cudaSuccess);
   if (!(K[0] > 0.0) || !(K[1] > 0.0)) return mf::host_fail(MF_ERR_INVALID_ARG, "fx, fy must be > 0", cudaSuccess);
+  // every pointer must be device memory of the current device: the kernels
+  // run there, and another GPU's memory would fault them
+  int dev = -1;
+  cudaError_t de = cudaGetDevice(&dev);
+  if (de != cudaSuccess) return mf::host_fail(MF_ERR_NO_DEVICE, "cudaGetDevice", de);
   const void* ptrs[5] = {poses_w2c_3x4, depth, focus_map, guided_depth, info};
   for (const void* p : ptrs)
-    if (p && !on_device(p))
-      return mf::host_fail(MF_ERR_INVALID_ARG, "mf_render_noalloc takes device pointers only", cudaSuccess);
+    if (p && mf::host_pointer_kind(p, dev) != mf::kPtrDevice)
+      return mf::host_fail(MF_ERR_INVALID_ARG,
+                           "mf_render_noalloc takes device pointers of the current device only",
+                           cudaSuccess);
 
   double w[MF_MAX_HISTORY] = {};
   if (!mf::host_ls_weights(d->smooth_len, d->mode, w))

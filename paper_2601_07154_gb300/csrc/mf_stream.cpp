@@ -14,6 +14,9 @@
 #include <string>
 #include <thread>
 #include <utility>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "mf_internal.h"
@@ -66,14 +69,14 @@ struct DeviceGuard {
   }
 };
 
-bool is_device_ptr(const void* p) {
-  if (!p) return false;
+int pointer_kind(const void* p, int dev) {
+  if (!p) return mf::kPtrHost;
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return mf::kPtrHost;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  return mf::classify_pointer((int)a.type, a.device, dev);
 }
 
 // Exact least-squares derivative weights (Eqs. 2-3 generalised): the K
@@ -494,6 +497,32 @@ int host_validate_desc(const mf_stream_desc* d) { return validate_desc(d); }
 int host_map_path(uint32_t flags) { return map_path(flags); }
 int host_fail(int status, const char* what, cudaError_t e) { return fail(status, what, e); }
 void host_count_launches(int64_t n) { g_launches.fetch_add(n); }
+int host_pointer_kind(const void* p, int dev) { return pointer_kind(p, dev); }
+
+KernelFit host_kernel_fit(const void* kernel, int threads, size_t smem_limit, size_t smem_launch,
+                          int carveout) {
+  static std::mutex mu;
+  static std::map<std::tuple<const void*, int, size_t, size_t>, KernelFit> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const auto key = std::make_tuple(kernel, dev, smem_limit, smem_launch);
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  KernelFit f;
+  cudaDeviceGetAttribute(&f.sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_limit);
+  if (carveout >= 0) cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, carveout);
+  int per = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem_launch) != cudaSuccess) {
+    cudaGetLastError();
+    per = 1;
+  }
+  f.per_sm = per < 1 ? 1 : per;
+  if (f.sms < 1) f.sms = 1;
+  cache.emplace(key, f);
+  return f;
+}
 }  // namespace mf
 
 extern "C" {
@@ -597,7 +626,11 @@ int mf_push_frames(mf_stream* s, int32_t n, const double* poses, const void* dep
   // Poses: device pointers are read in place; host poses go through a pinned
   // bounce buffer so the caller may reuse its memory at once.
   const double* pdev = poses;
-  if (!is_device_ptr(poses)) {
+  const int pose_kind = pointer_kind(poses, s->device);
+  const int depth_kind = pointer_kind(depth, s->device);
+  if (pose_kind == mf::kPtrOtherDevice || depth_kind == mf::kPtrOtherDevice)
+    return fail(MF_ERR_INVALID_ARG, "poses or depth live on another GPU than the stream's device");
+  if (pose_kind != mf::kPtrDevice) {
     if ((int64_t)n > s->pose_dev_cap) {
       const int64_t cap = pow2_at_least(std::max<int64_t>(n, 256));
       double* nd = (double*)s->dalloc((size_t)cap * 12 * sizeof(double));
@@ -629,7 +662,7 @@ int mf_push_frames(mf_stream* s, int32_t n, const double* poses, const void* dep
   std::vector<Run> new_runs;
   if (depth) {
     const char* dsrc = static_cast<const char*>(depth) + (size_t)O * s->plane_in;
-    if (is_device_ptr(depth)) {
+    if (depth_kind == mf::kPtrDevice) {
       new_runs.push_back(Run{s->emitted, n_emit, dsrc, 0, nullptr});
     } else {
       rc = ensure_stage(s, n_emit);
@@ -712,10 +745,15 @@ int mf_get_maps(mf_stream* s, int32_t max_frames, void* focus_map, void* guided_
   DeviceGuard guard(s->device);
   LaunchTally tally(&s->launches);
 
-  const bool m_host = focus_map && !is_device_ptr(focus_map);
-  const bool g_host = guided_depth && !is_device_ptr(guided_depth);
-  const bool i_host = info && !is_device_ptr(info);
-  const bool p_host = points && !is_device_ptr(points);
+  const int kinds[4] = {pointer_kind(focus_map, s->device), pointer_kind(guided_depth, s->device),
+                        pointer_kind(info, s->device), pointer_kind(points, s->device)};
+  for (int k : kinds)
+    if (k == mf::kPtrOtherDevice)
+      return fail(MF_ERR_INVALID_ARG, "an output lives on another GPU than the stream's device");
+  const bool m_host = focus_map && kinds[0] != mf::kPtrDevice;
+  const bool g_host = guided_depth && kinds[1] != mf::kPtrDevice;
+  const bool i_host = info && kinds[2] != mf::kPtrDevice;
+  const bool p_host = points && kinds[3] != mf::kPtrDevice;
   const bool maps_host = m_host || g_host;
   // Maps bound for host memory are rendered in pieces into a ring of
   // kOutSlots staging pieces; each piece's download on st_out overlaps the

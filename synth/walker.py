@@ -54,6 +54,9 @@ class WalkerSpec:
     turn_rate_deg: float = 45.0   # |yaw rate| bound for turns
     turn_seg_s: tuple = (1.0, 3.0)
     climb: float = 0.0            # vertical speed in m/s (negative y is up)
+    accel: float = 0.0            # forward acceleration magnitude, m/s^2 (0: constant speed)
+    accel_seg_s: tuple = (1.0, 2.5)
+    speed_range: tuple = (0.5, 3.0)
     seed: int = 1
 
 
@@ -101,12 +104,33 @@ def walk(spec: WalkerSpec) -> Trajectory:
             rates[lo:hi] = rate
             t0 += dur
 
+    # forward speed: constant, or (accel > 0) speeding up and slowing down in
+    # turn, in segments of seeded length and rate (a scooter or a runner
+    # changing pace), kept within speed_range.  Its draws come from a stream
+    # of their own, so constant-speed walkers are unchanged.
+    speeds = np.full(n, spec.speed)
+    if spec.accel > 0.0:
+        arng = Xoshiro256ss(spec.seed * 2 + (1 << 40))
+        acc = np.zeros(n)
+        t0, sign = 0.0, 1.0
+        while t0 < n * dt:
+            dur = arng.uniform(*spec.accel_seg_s)
+            a = sign * spec.accel * arng.uniform(0.6, 1.0)
+            lo = int(math.ceil(t0 / dt))
+            hi = min(n, int(math.ceil((t0 + dur) / dt)))
+            acc[lo:hi] = a
+            t0 += dur
+            sign = -sign
+        lo_v, hi_v = spec.speed_range
+        for k in range(1, n):
+            speeds[k] = min(hi_v, max(lo_v, speeds[k - 1] + acc[k - 1] * dt))
+
     body_yaw = np.zeros(n)
     body_pos = np.zeros((n, 3))
     for k in range(1, n):
         body_yaw[k] = body_yaw[k - 1] + rates[k - 1] * dt
         psi = body_yaw[k - 1]
-        step = spec.speed * dt
+        step = speeds[k - 1] * dt
         body_pos[k] = body_pos[k - 1] + np.array(
             [step * math.sin(psi), -spec.climb * dt, step * math.cos(psi)])
 

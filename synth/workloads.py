@@ -90,14 +90,18 @@ def small_stream(seed=1, n_frames=64, window=8, smooth_len=15):
                           (260.0, 260.0, 160.0, 120.0), spec)
 
 
-def hd_stream(seed=2, n_frames=900, window=16, smooth_len=15, ring=8):
-    spec = WalkerSpec(n_frames=n_frames, seed=seed, turns=True)
-    return StreamWorkload("1920x1080x900", 1920, 1080, n_frames, window, smooth_len,
+def hd_stream(seed=2, n_frames=900, window=16, smooth_len=15, ring=8, accel=0.0):
+    """``accel`` > 0 adds forward speed changes of up to that many m/s^2, so
+    that ACCEL-mode motion points land in view."""
+    spec = WalkerSpec(n_frames=n_frames, seed=seed, turns=True, accel=accel)
+    name = f"1920x1080x{n_frames}" + (f"_accel{accel:g}" if accel else "")
+    return StreamWorkload(name, 1920, 1080, n_frames, window, smooth_len,
                           (1500.0, 1500.0, 960.0, 540.0), spec, ring=ring)
 
 
-def mixed_streams(n_streams=64, cfg=4, ring=8, smooth_len=15, max_frames=None):
-    """Seeded mixed-resolution streams; stream s uses seed 1000*cfg + s."""
+def mixed_streams(n_streams=64, cfg=4, ring=8, smooth_len=15, max_frames=None, accel=0.0):
+    """Seeded mixed-resolution streams; stream s uses seed 1000*cfg + s.
+    ``accel`` > 0 gives every walker forward speed changes (see hd_stream)."""
     out = []
     for s in range(n_streams):
         seed = 1000 * cfg + s
@@ -108,7 +112,7 @@ def mixed_streams(n_streams=64, cfg=4, ring=8, smooth_len=15, max_frames=None):
             n = min(n, max_frames)
         win = int(rng.uniform(8, 33))
         f = rng.uniform(0.7, 1.2) * w
-        spec = WalkerSpec(n_frames=n, seed=seed, turns=True)
+        spec = WalkerSpec(n_frames=n, seed=seed, turns=True, accel=accel)
         out.append(StreamWorkload(f"{w}x{h}x{n}", w, h, n, win, smooth_len,
                                   (f, f, w / 2.0, h / 2.0), spec, ring=ring))
     return out

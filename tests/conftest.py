@@ -1,3 +1,4 @@
+import json
 import os
 import sys
 
@@ -8,3 +9,14 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
+
+
+def pytest_terminal_summary(terminalreporter, exitstatus, config):
+    """The largest GPU-vs-oracle coordinate errors of the session (pixels)."""
+    parity = sys.modules.get("tests.parity")
+    if parity is None:
+        return
+    rec = {k: {"max_du_px": v[0], "max_dv_px": v[1], "points": v[2]}
+           for k, v in parity.COORD_ERR.items() if v[2]}
+    if rec:
+        terminalreporter.write_line("COORD_ERROR " + json.dumps(rec))

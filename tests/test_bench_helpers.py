@@ -9,21 +9,26 @@ import sys
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 sys.path.insert(0, ROOT)
 
+import pytest  # noqa: E402
+
 import bench  # noqa: E402
 
 
-def test_profiled_traffic_needs_the_profiled_sources(tmp_path, monkeypatch):
+@pytest.mark.parametrize("workload", ["default", "heading"])
+def test_profiled_traffic_needs_the_profiled_sources(tmp_path, monkeypatch, workload):
     kernel = "map_stream_kernel"
+    key = (kernel, workload)
     per_frame = 19_000_000
     prof = tmp_path / "p.txt"
-    prof.write_text(f"source_sha256_16: {bench.map_source_hash(kernel)}\n"
+    prof.write_text(f"source_sha256_16: {bench.map_source_hash(key)}\n"
                     f"dram_bytes_per_frame: {per_frame}\n")
-    monkeypatch.setitem(bench.PROFILES, kernel, (str(prof), bench.PROFILES[kernel][1]))
+    monkeypatch.setitem(bench.PROFILES, key, (str(prof), bench.PROFILES[key][1]))
     # the lookup joins profiles/ to the name; an absolute name stays as given
-    assert bench.profiled_traffic(900, kernel) == per_frame * 900
+    assert bench.profiled_traffic(900, kernel, workload) == per_frame * 900
     prof.write_text("source_sha256_16: 0000000000000000\ndram_bytes_per_frame: 1\n")
-    assert bench.profiled_traffic(900, kernel) is None
+    assert bench.profiled_traffic(900, kernel, workload) is None
     assert bench.profiled_traffic(900, "no_such_kernel") is None
+    assert bench.profiled_traffic(900, kernel, "no_such_workload") is None
 
 
 def test_committed_profiles_name_their_sources():
@@ -37,6 +42,9 @@ def test_committed_profiles_name_their_sources():
 def test_workload_config_and_frame_bytes():
     cfg = bench.workload_config()
     assert cfg["width"] == 1920 and cfg["height"] == 1080 and cfg["frames_per_step"] == 900
+    assert "ACCEL" in cfg["workload"] and "speed changes" not in cfg["workload"]
+    assert "HEADING" in bench.workload_config(workload="heading")["workload"]
+    assert "speed changes" in bench.workload_config(workload="accel_in_view")["workload"]
     assert bench.FRAME_BYTES == 1920 * 1080 * 12
     assert 1 <= bench.PIECE_FRAMES <= 64
 
@@ -50,4 +58,5 @@ def test_reference_arm_prints_one_line_on_the_host():
     rec = json.loads(out[-1])
     assert rec["impl"] == "reference" and rec["unit"] == "frames/s" and rec["value"] > 0
     assert rec["cpu_baseline"]["kind"] == "oracle" and rec["e2e"]["value"] == rec["value"]
+    assert rec["cpu_baseline"]["cores"] == (os.cpu_count() or 1)
     assert rec["e2e"]["h2d_bytes_per_step"] == 0 and rec["higher_is_better"] is True

@@ -100,3 +100,42 @@ def test_server_queue_limit_and_unknown_stream(mf):
         srv.submit(1, P, None, K)                # slot 1 was never admitted
     assert e.value.status == mf.MF_ERR_INVALID_ARG
     srv.close()                                  # stops with queued work: no hang
+
+
+def test_latency_probe_stamps_after_the_work(mf):
+    """mf_probe_stamp: the completion stamp of the plain per-stream path.  A
+    stamp enqueued behind a stream's map rendering completes after it, and
+    each frame's latency runs from its own arrival time."""
+    dev = torch.device("cuda", 0)
+    spec = STREAMS[0]
+    width, height, window, smooth_len, mode, seed, frames = spec
+    poses, depth, K = _inputs(spec)
+    st = torch.cuda.Stream(dev)
+    s = mf.MotionFocusStream(width, height, window=window, smooth_len=smooth_len, mode=mode,
+                             device=dev, cuda_stream=st)
+    p = mf._mf.mf_probe_open()
+    D = torch.from_numpy(depth).to(dev)
+    torch.cuda.synchronize()
+    t_before = mf.mf_clock_ns()
+    arrivals = np.array([t_before - 1_000_000 * k for k in range(frames)], dtype=np.int64)
+    s.push(torch.from_numpy(poses).to(dev), D, K)
+    M, G, info, _ = s.get_maps()
+    mf._mf.mf_probe_stamp(p, st.cuda_stream, arrivals)
+    st.synchronize()
+    t_after = mf.mf_clock_ns()
+    # the host function may still be running just after the stream's work
+    for _ in range(1000):
+        lat = mf._mf.mf_probe_latency(p)
+        if lat.frames == frames:
+            break
+        torch.cuda.synchronize()
+    assert lat.frames == frames
+    span_ms = (t_after - t_before) * 1e-6
+    # frame k arrived k ms before t_before: its latency is k ms plus the work
+    assert 0.0 < lat.p50_ms and lat.max_ms <= (frames - 1) + span_ms + 50.0
+    assert lat.max_ms >= frames - 1
+    empty = mf._mf.mf_probe_latency(p, reset=True)
+    assert empty.frames == frames
+    assert mf._mf.mf_probe_latency(p).frames == 0
+    mf._mf.mf_probe_close(p)
+    s.close()
