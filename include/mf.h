@@ -74,7 +74,10 @@ typedef enum {
 typedef enum {
   MF_FRAME_OK = 0,        /* at least one valid motion point */
   MF_FRAME_EMPTY = 1,     /* no valid motion point: M = G = 0 */
-  MF_FRAME_BAD_POSE = 2   /* the frame's own pose is not a rigid transform */
+  MF_FRAME_BAD_POSE = 2,  /* the frame's own pose is not a rigid transform */
+  MF_FRAME_TIMEOUT = 3    /* a bounded device wait of the tensor-core map kernel ran
+                             out while rendering this frame: bands of its maps hold NaN
+                             (the waiting call also returns MF_ERR_TIMEOUT) */
 } mf_frame_status;
 
 /* The normaliser Z of Eq. 7, which the paper leaves open:
@@ -283,6 +286,28 @@ int64_t mf_total_kernel_launches(void);
 /* Text of the last error raised on the calling thread ("" if none); valid
  * until the thread's next failing call. */
 const char* mf_last_error(void);
+
+/* Host-side fault injection, for testing how callers detect failures.  The
+ * paper has no counterpart.  Every fault is made on the host at a chosen
+ * call; none makes a GPU fault, trap or hang.  `spec` is a comma-separated
+ * list of rules, each a name with an optional "@n" (the n-th occurrence
+ * fails, counted from this call; without it every occurrence fails):
+ *   alloc_fail      a device allocation of a stream or an engine returns
+ *                   nothing (the call reports MF_ERR_OOM);
+ *   bad_pose        a host pose of mf_push_frames is scaled so that it is no
+ *                   rotation on its way to the device (its frame reports
+ *                   MF_FRAME_BAD_POSE); occurrences count poses;
+ *   drop_push       a serving push is accepted and then lost: its frames never
+ *                   complete (mf_server_drain with a timeout returns
+ *                   MF_ERR_TIMEOUT; mf_server_frames_done falls short);
+ *   admission_full  an engine or server admission is refused (MF_ERR_ADMISSION);
+ *   wait_timeout    a completed mf_sync / mf_get_maps wait reports a device
+ *                   wait that ran out (MF_ERR_TIMEOUT), as the tensor-core map
+ *                   kernel's bounded wait does when it expires.
+ * NULL or "" removes every rule.  The environment variable MF_FAULT, read
+ * at the first use, installs an initial spec.  Returns MF_ERR_INVALID_ARG for
+ * a malformed spec (the rules in force are then unchanged). */
+int mf_set_fault(const char* spec);
 
 /* ---------------------------------------------------------------------------
  * Batched engine: many streams on one GPU, one batched launch per tick.

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libmf.so")
 MF_F32, MF_BF16, MF_F16 = 0, 1, 2
 MF_MODE_ACCEL, MF_MODE_HEADING = 0, 1
 MF_POSES_WORLD, MF_POSES_BATCH_LOCAL = 0, 1
-MF_FRAME_OK, MF_FRAME_EMPTY, MF_FRAME_BAD_POSE = 0, 1, 2
+MF_FRAME_OK, MF_FRAME_EMPTY, MF_FRAME_BAD_POSE, MF_FRAME_TIMEOUT = 0, 1, 2, 3
 MF_FLAG_TIME_KERNELS = 1
 MF_FLAG_MAP_CUDA_CORES = 8
 MF_FLAG_MAP_TENSOR_CORES = 16
@@ -36,7 +36,8 @@ EXPORTED = ("mf_stream_desc_init", "mf_open_stream", "mf_push_frames", "mf_get_m
             "mf_server_frames_done", "mf_server_remove_stream", "mf_server_drain",
             "mf_server_latency", "mf_server_get_stats", "mf_server_close", "mf_clock_ns",
             "mf_engine_submit_batch", "mf_server_submit_batch", "mf_server_tune",
-            "mf_probe_open", "mf_probe_stamp", "mf_probe_latency", "mf_probe_close")
+            "mf_probe_open", "mf_probe_stamp", "mf_probe_latency", "mf_probe_close",
+            "mf_set_fault")
 MF_ENGINE_NO_GRAPH = 2
 MF_ENGINE_NO_TUNE = 4
 MF_NOALLOC_MAX_FRAMES = 256
@@ -184,6 +185,7 @@ def _load():
     lib.mf_probe_stamp.argtypes = [vp, vp, i32, vp]
     lib.mf_probe_latency.argtypes = [vp, ctypes.POINTER(MFLatencyStats), i32]
     lib.mf_probe_close.argtypes = [vp]
+    lib.mf_set_fault.argtypes = [ctypes.c_char_p]
     for name in ("mf_open_stream", "mf_push_frames", "mf_get_maps", "mf_sync",
                  "mf_pending_frames", "mf_reset_stream", "mf_stream_stats", "mf_close_stream",
                  "mf_render_noalloc", "mf_engine_open", "mf_engine_add_stream",
@@ -194,7 +196,7 @@ def _load():
                  "mf_server_remove_stream", "mf_server_drain", "mf_server_latency",
                  "mf_server_get_stats", "mf_server_close", "mf_engine_submit_batch",
                  "mf_server_submit_batch", "mf_server_tune", "mf_probe_open", "mf_probe_stamp",
-                 "mf_probe_latency", "mf_probe_close"):
+                 "mf_probe_latency", "mf_probe_close", "mf_set_fault"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -483,3 +485,9 @@ def mf_probe_latency(p, reset=False):
 
 def mf_probe_close(p):
     _check(lib.mf_probe_close(p), "mf_probe_close")
+
+
+# ------------------------------------------------------- fault injection --
+def mf_set_fault(spec=None):
+    """Host-side fault injection rules (see include/mf.h); None clears them."""
+    _check(lib.mf_set_fault(spec.encode() if spec else None), "mf_set_fault")

@@ -180,6 +180,7 @@ struct mf_engine {
 
   void* dalloc(size_t n) {
     void* p = nullptr;
+    if (mf::fault_fires(mf::kFaultAllocFail)) return nullptr;
     if (cudaMalloc(&p, n) != cudaSuccess) {
       cudaGetLastError();
       return nullptr;
@@ -634,6 +635,8 @@ int mf_engine_add_stream(mf_engine* e, const mf_stream_desc* d, int64_t reserve_
       break;
     }
   if (free_slot < 0) return fail(MF_ERR_ADMISSION, "every stream slot is taken");
+  if (mf::fault_fires(mf::kFaultAdmissionFull))
+    return fail(MF_ERR_ADMISSION, "admission refused (injected fault)");
   // the slot's history is part of the engine's memory already; the budget
   // admits the caller's reservation on top of it
   if (e->d.memory_budget > 0 && e->accounted() + reserve_bytes > e->d.memory_budget)

@@ -16,8 +16,8 @@
 namespace {
 
 struct FaultRule {
-  bool on = false;
-  int64_t at = 0;       // 1-based occurrence that fires (0: every one)
+  std::atomic<bool> on{false};
+  std::atomic<int64_t> at{0};  // 1-based occurrence that fires (0: every one)
   std::atomic<int64_t> seen{0};
 };
 
@@ -65,9 +65,10 @@ bool parse(const char* spec, bool (&on)[mf::kFaultKinds], int64_t (&at)[mf::kFau
 
 void install(const bool (&on)[mf::kFaultKinds], const int64_t (&at)[mf::kFaultKinds]) {
   for (int k = 0; k < mf::kFaultKinds; ++k) {
+    g_rules[k].on.store(false);
     g_rules[k].seen.store(0);
-    g_rules[k].at = at[k];
-    g_rules[k].on = on[k];
+    g_rules[k].at.store(at[k]);
+    g_rules[k].on.store(on[k]);
   }
 }
 
@@ -82,9 +83,10 @@ void load_env() {
 bool mf::fault_fires(int kind) {
   std::call_once(g_env_once, load_env);
   FaultRule& r = g_rules[kind];
-  if (!r.on) return false;
+  if (!r.on.load(std::memory_order_acquire)) return false;
   const int64_t n = r.seen.fetch_add(1) + 1;
-  return r.at == 0 || n == r.at;
+  const int64_t at = r.at.load();
+  return at == 0 || n == at;
 }
 
 extern "C" int mf_set_fault(const char* spec) {

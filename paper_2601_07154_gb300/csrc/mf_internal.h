@@ -89,6 +89,9 @@ struct MapParams {
   // Work counter of the persistent map kernels' dynamic unit schedule: 0 at
   // launch and left at 0; no two launches in flight may share it.
   unsigned int* sched;
+  // Set to 1 by a kernel whose bounded device wait ran out (device-visible;
+  // may be NULL).  The frames concerned are also marked MF_FRAME_TIMEOUT.
+  unsigned int* fault;
 };
 
 // MF_NORM_MAX applies to frames whose count-normalised map maximum is at

@@ -204,6 +204,14 @@ __device__ __forceinline__ void fetch_depth(TIn* sD, const TIn* dplane, int widt
   cp_async_commit();
 }
 
+// A bounded wait that ran out: the frame's record is marked and the launch's
+// fault word set, so the host reports MF_ERR_TIMEOUT instead of returning the
+// NaN-filled bands silently.
+__device__ __forceinline__ void report_wait_expired(const MapParams& p, const FrameRec* rec) {
+  atomicExch(reinterpret_cast<int*>(const_cast<int32_t*>(&rec->status)), (int)MF_FRAME_TIMEOUT);
+  if (p.fault) atomicExch_system(p.fault, 1u);
+}
+
 __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t phase) {
   uint32_t done = 0;
   for (long long it = 0; it < kTcWaitPolls && !done; ++it)
@@ -348,6 +356,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) map_tc_kernel(MapParams p, int 
         }
         __syncthreads();  // every thread's part of depth tile b has landed
         ok = wait_bar(&mma_bar[cur], cur ? phase1 : phase0);
+        if (!ok) report_wait_expired(p, rec);
         if (cur)
           phase1 ^= 1u;
         else

@@ -27,11 +27,14 @@ constexpr size_t kPoseOff = (kRecBytes + 255) / 256 * 256;
 constexpr size_t kPoseBytes = sizeof(double) * 12 * kRingSlots;
 constexpr size_t kBadOff = kPoseOff + (kPoseBytes + 255) / 256 * 256;
 constexpr size_t kSchedOff = kBadOff + (sizeof(int32_t) * kRingSlots + 255) / 256 * 256;
-constexpr size_t kScratchBytes = kSchedOff + sizeof(unsigned int);
+constexpr size_t kFaultOff = kSchedOff + sizeof(unsigned int);
+constexpr size_t kScratchBytes = kFaultOff + sizeof(unsigned int);
 
 // The shared scratch: frame records, then pose copies, then rigidity flags,
 // then the map kernels' work counter (zero from load, and every map launch
-// leaves it at zero).
+// leaves it at zero), then the fault word a map kernel sets when a bounded
+// device wait runs out (this entry point reports that per frame, as
+// MF_FRAME_TIMEOUT in the records).
 static __device__ __align__(256) unsigned char mf_noalloc_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
@@ -160,6 +163,7 @@ extern "C" int mf_render_noalloc(const mf_stream_desc* d, int32_t n_poses,
     mp.d0 = (float)d->depth_ref_m;
     mp.path = mf::host_map_path(d->flags);
     mp.sched = sched;
+    mp.fault = reinterpret_cast<unsigned int*>(scratch + kFaultOff);
     e = mf::launch_map(mp, d->window, d->depth_dtype, d->map_dtype, d->normalize, st, &launches);
   }
   if (e == cudaSuccess && info) {

@@ -196,6 +196,13 @@ int enqueue(mf_server* s, const mf_push& p, int64_t t_now) {
   if (p.n <= O) return fail(MF_ERR_INVALID_ARG, "batch must hold more frames than the overlap");
   if (p.n - O > s->d.engine.max_stream_frames)
     return fail(MF_ERR_INVALID_ARG, "push exceeds max_stream_frames");
+  if (mf::fault_fires(mf::kFaultDropPush)) {
+    // injected fault: the push is accepted and lost, so its frames never
+    // complete (drain with a timeout and frames_done detect it)
+    ++sl.pushes;
+    sl.frames_submitted += p.n - O;
+    return MF_OK;
+  }
   QueuedPush q;
   q.t_submit = p.arrival_ns ? p.arrival_ns : t_now;
   q.n = p.n;

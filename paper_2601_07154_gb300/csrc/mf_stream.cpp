@@ -206,6 +206,10 @@ struct mf_stream {
   FrameRec* recs = nullptr;
   int64_t rec_cap = 0;
   unsigned int* sched = nullptr;  // map kernels' work counter
+  // Fault word in mapped page-locked host memory: a map kernel whose bounded
+  // device wait runs out sets it; the next completed wait reports it.
+  unsigned int* fault_host = nullptr;
+  unsigned int* fault_dev = nullptr;
 
   double* pose_dev = nullptr;      // device staging of host poses
   int64_t pose_dev_cap = 0;
@@ -237,6 +241,7 @@ struct mf_stream {
 
   void* dalloc(size_t bytes) {
     void* p = nullptr;
+    if (mf::fault_fires(mf::kFaultAllocFail)) return nullptr;
     if (d.dev_alloc) {
       p = d.dev_alloc(bytes, d.alloc_ctx);
     } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
@@ -373,6 +378,16 @@ int ensure_out_stage(mf_stream* s, size_t bytes) {
   return MF_OK;
 }
 
+// A completed wait on the stream reports a device wait that ran out in a map
+// kernel since the last report (the fault word), or one injected on the host.
+int check_fault(mf_stream* s) {
+  if (mf::fault_fires(mf::kFaultWaitTimeout)) *reinterpret_cast<volatile unsigned int*>(s->fault_host) = 1u;
+  if (__atomic_exchange_n(s->fault_host, 0u, __ATOMIC_ACQ_REL) == 0u) return MF_OK;
+  return fail(MF_ERR_TIMEOUT,
+              "a bounded device wait of the tensor-core map kernel ran out: the frames concerned are "
+              "marked MF_FRAME_TIMEOUT and bands of their maps hold NaN");
+}
+
 int wait_event(cudaEvent_t ev, int64_t timeout_ns) {
   const auto t0 = std::chrono::steady_clock::now();
   int spins = 0;
@@ -441,6 +456,7 @@ void destroy(mf_stream* s) {
   s->dfree(s->stage, (size_t)s->stage_slots * s->plane_in);
   s->dfree(s->out_stage, s->out_stage_bytes);
   if (s->pose_host) cudaFreeHost(s->pose_host);
+  if (s->fault_host) cudaFreeHost(s->fault_host);
   if (s->pose_ev) cudaEventDestroy(s->pose_ev);
   if (s->done_ev) cudaEventDestroy(s->done_ev);
   if (s->own_stream && s->st) cudaStreamDestroy(s->st);
@@ -588,6 +604,13 @@ int mf_open_stream(const mf_stream_desc* d, mf_stream** out) {
     destroy(s);
     return fail(MF_ERR_OOM, "frame record or work counter allocation failed");
   }
+  if (cudaHostAlloc((void**)&s->fault_host, sizeof(unsigned int), cudaHostAllocMapped) != cudaSuccess ||
+      cudaHostGetDevicePointer((void**)&s->fault_dev, s->fault_host, 0) != cudaSuccess) {
+    cudaGetLastError();
+    destroy(s);
+    return fail(MF_ERR_OOM, "fault word allocation failed");
+  }
+  *s->fault_host = 0u;
   // every map launch of the stream leaves its counter at 0 again
   if (cudaMemsetAsync(s->sched, 0, sizeof(unsigned int), s->st) != cudaSuccess) {
     cudaGetLastError();
@@ -651,6 +674,8 @@ int mf_push_frames(mf_stream* s, int32_t n, const double* poses, const void* dep
       s->pose_host_cap = cap;
     }
     std::memcpy(s->pose_host, poses, (size_t)n * 12 * sizeof(double));
+    for (int32_t k = 0; k < n; ++k)  // injected fault: a pose that is no rotation
+      if (mf::fault_fires(mf::kFaultBadPose)) s->pose_host[(size_t)k * 12] *= 2.0;
     MF_CUDA(cudaMemcpyAsync(s->pose_dev, s->pose_host, (size_t)n * 12 * sizeof(double),
                             cudaMemcpyHostToDevice, s->st),
             "pose upload");
@@ -853,6 +878,7 @@ int mf_get_maps(mf_stream* s, int32_t max_frames, void* focus_map, void* guided_
     mp.d0 = (float)s->d.depth_ref_m;
     mp.path = map_path(s->d.flags);
     mp.sched = s->sched;
+    mp.fault = s->fault_dev;
     TimerPair tp{};
     if (timed) {
       rc = timer_pair(s, &tp);
@@ -919,7 +945,8 @@ int mf_get_maps(mf_stream* s, int32_t max_frames, void* focus_map, void* guided_
     if (rc) return rc;
     for (int k = 0; k < kOutSlots; ++k) s->slot_busy[k] = false;
     MF_CUDA(cudaEventRecord(s->done_ev, s->st), "event record");
-    return wait_event(s->done_ev, timeout_ns);
+    rc = wait_event(s->done_ev, timeout_ns);
+    return rc ? rc : check_fault(s);
   }
   return MF_OK;
 }
@@ -928,7 +955,8 @@ int mf_sync(mf_stream* s, int64_t timeout_ns) {
   if (!s) return fail(MF_ERR_INVALID_ARG, "NULL stream");
   DeviceGuard guard(s->device);
   MF_CUDA(cudaEventRecord(s->done_ev, s->st), "event record");
-  return wait_event(s->done_ev, timeout_ns);
+  const int rc = wait_event(s->done_ev, timeout_ns);
+  return rc ? rc : check_fault(s);
 }
 
 int mf_pending_frames(const mf_stream* s, int32_t* n) {

@@ -76,3 +76,16 @@ def test_struct_layouts_match_the_header(mf):
     assert mf._mf.PUSH_DTYPE.itemsize == 64
     assert mf._mf.MF_FLAG_MAP_CUDA_CORES & mf._mf.MF_FLAG_MAP_TENSOR_CORES == 0
     assert (mf._mf.MF_FLAG_MAP_CUDA_CORES | mf._mf.MF_FLAG_MAP_TENSOR_CORES) & mf._mf.MF_FLAG_TIME_KERNELS == 0
+
+
+def test_fault_spec_parsing(mf):
+    """mf_set_fault accepts rule lists and refuses malformed ones without
+    changing the rules in force (host only: no rule fires here)."""
+    for spec in ("alloc_fail", "alloc_fail@2", "bad_pose@5,drop_push@1", "admission_full,wait_timeout@3",
+                 "", None):
+        mf.mf_set_fault(spec)
+    for spec in ("nope", "alloc_fail@0", "alloc_fail@", "alloc_fail@x", "bad_pose@-1", "@3"):
+        with pytest.raises(mf.MFError) as e:
+            mf.mf_set_fault(spec)
+        assert e.value.status == mf.MF_ERR_INVALID_ARG, spec
+    mf.mf_set_fault(None)
