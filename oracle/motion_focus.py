@@ -45,7 +45,14 @@ path's specification):
 * motion-guided depth G = M * min(1, d0 / D) for finite D > 0, else 0;
 * poses whose rotation is not orthonormal to 1e-6 (or that are not finite)
   are "bad": a frame with a bad pose is empty, and a point whose K-sample fit
-  touches a bad pose is invalid.
+  touches a bad pose is invalid;
+* depth alignment across batches (Section 2.2, Fig. 3 caption; optional):
+  every batch-local batch after the first gets one scale s_b = s_{b-1} * m,
+  m = the lower median of the single-precision ratios D_prev / D_cur over the
+  overlap frames' pixels where both depths are finite and > 0 (s_0 = 1; no
+  such pixel: m = 1).  The batch's translations are multiplied by s_b before
+  anchoring and its depth by s_b in the guided depth, so that batches a
+  monocular model returns at different scales share the first batch's.
 """
 import math
 from dataclasses import dataclass
@@ -84,6 +91,7 @@ class Params:
     s_hi: float = 4.0
     depth_ref_m: float = 1.0
     normalize: str = "count"    # Z of Eq. 7: "count" (valid points) or "max" (map maximum)
+    depth_align: bool = False   # batch-local only: one depth scale per batch (Section 2.2)
 
 
 # Z = map maximum applies to maps whose count-normalised maximum is at least
@@ -188,6 +196,20 @@ def anchor_transform(T_anchor_world, L_anchor_local):
     H[:3, :3] = Ry
     H[:3, 3] = c_world - Ry @ c_local
     return H
+
+
+def depth_scale_ratio(prev, cur):
+    """Depth alignment of two batches over their shared frames (Section 2.2,
+    Fig. 3): the lower median (sorted[(n-1)//2]) of the ratios prev / cur,
+    each an IEEE single-precision quotient, over the pixels where both depths
+    are finite and > 0; None when no pixel qualifies."""
+    a = np.asarray(prev, dtype=np.float32).ravel()
+    b = np.asarray(cur, dtype=np.float32).ravel()
+    ok = np.isfinite(a) & np.isfinite(b) & (a > 0) & (b > 0)
+    if not ok.any():
+        return None
+    r = np.sort(np.divide(a[ok], b[ok], dtype=np.float32))
+    return float(r[(r.size - 1) // 2])
 
 
 # -------------------------------------------------------------- Eqs. 5-6 --
@@ -345,7 +367,10 @@ class OracleStream:
         self.bad = []
         self.K = []         # intrinsics in force for each emitted frame
         self.depth = []     # depth image of each emitted frame (or None)
+        self.scale = []     # depth alignment scale of each emitted frame
         self.pushes = 0
+        self.batch_scale = 1.0      # s of the last batch
+        self.overlap_depth = None   # that batch's last `overlap` depth planes
 
     def push(self, poses, depth, K):
         """Ingest one batch of n poses (n,3,4) and depth (n,H,W); returns #emitted."""
@@ -356,6 +381,18 @@ class OracleStream:
         O = p.overlap if (local and self.pushes > 0) else 0
         if n <= O:
             raise ValueError("a batch must hold more frames than the overlap")
+        s_b = 1.0
+        if local and p.depth_align:
+            if self.pushes > 0:
+                m = None
+                if depth is not None and self.overlap_depth is not None and O > 0:
+                    m = depth_scale_ratio(self.overlap_depth, np.asarray(depth)[:O])
+                s_b = self.batch_scale * (m if m is not None else 1.0)
+            poses = poses.copy()
+            poses[:, :, 3] *= s_b       # the batch's translations in the first batch's scale
+            self.batch_scale = s_b
+            self.overlap_depth = (None if depth is None or p.overlap == 0
+                                  else np.asarray(depth)[n - p.overlap:].copy())
         rigid = [is_rigid(T) for T in poses]
         if local and self.pushes > 0:
             a = O - 1
@@ -376,6 +413,7 @@ class OracleStream:
             self.bad.append(b)
             self.K.append(np.asarray(K, dtype=np.float64).copy())
             self.depth.append(None if depth is None else depth[k])
+            self.scale.append(s_b)
         self.pushes += 1
         return n - O
 
@@ -401,7 +439,9 @@ class OracleStream:
                 # Z = the map's largest point sum: the map peaks at exactly 1
                 M = M / M.max()
             if self.depth[n] is not None:
-                G = guided_depth(M, self.depth[n], p.depth_ref_m)
+                D = self.depth[n] if self.scale[n] == 1.0 else self.scale[n] * np.asarray(
+                    self.depth[n], dtype=np.float64)
+                G = guided_depth(M, D, p.depth_ref_m)
             ax, ay, mx = map_argmax(M, pts.n_valid)
             info.update(argmax_x=ax, argmax_y=ay, map_max=mx)
         return info, pts, M, G
