@@ -101,6 +101,21 @@ typedef enum { MF_NORM_COUNT = 0, MF_NORM_MAX = 1 } mf_norm;
  * names the default explicitly.  The flags are exclusive. */
 #define MF_FLAG_MAP_CUDA_CORES 8u
 #define MF_FLAG_MAP_TENSOR_CORES 16u
+/* Depth alignment across batches (Section 2.2, Fig. 3), MF_POSES_BATCH_LOCAL
+ * streams only: a monocular model returns every batch at its own scale, so
+ * each batch after the first gets one scale s_b = s_{b-1} * m, where m is
+ * the lower median of the single-precision ratios of the previous batch's
+ * last `overlap` depth planes to this batch's first `overlap` planes, over
+ * the pixels where both are finite and > 0 (no such pixel: m = 1; the first
+ * batch, and the first batch after mf_reset_stream, has s = 1).  The
+ * batch's translations are multiplied by s_b before anchoring, and its
+ * depth by s_b in the motion-guided depth (G = M min(1, d0 / (s_b D))).
+ * Needs every batch to hold at least `overlap` frames; the library keeps a
+ * copy of the last `overlap` depth planes (device memory) between pushes.
+ * The paper names the step but not its rule: this is the library's reading.
+ * Not available in the batched engine or the serving loop
+ * (MF_ERR_INVALID_ARG there). */
+#define MF_FLAG_DEPTH_ALIGN 32u
 
 /*
  * Stream descriptor.  Fill with mf_stream_desc_init() and override fields.
@@ -163,7 +178,8 @@ typedef struct {
   int32_t argmax_x, argmax_y;  /* largest M (ties: lowest y*width+x); -1 if empty */
   float map_max;               /* M at the argmax (FP32 arithmetic value, after
                                   the MF_NORM_MAX scaling when selected) */
-  int32_t reserved;
+  float depth_scale;           /* the frame's batch depth scale, rounded to FP32
+                                  (1 without MF_FLAG_DEPTH_ALIGN) */
 } mf_frame_info;
 
 /* One motion point (slot s of a frame), FP64 (40 bytes). */

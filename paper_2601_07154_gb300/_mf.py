@@ -21,6 +21,7 @@ MF_FRAME_OK, MF_FRAME_EMPTY, MF_FRAME_BAD_POSE, MF_FRAME_TIMEOUT = 0, 1, 2, 3
 MF_FLAG_TIME_KERNELS = 1
 MF_FLAG_MAP_CUDA_CORES = 8
 MF_FLAG_MAP_TENSOR_CORES = 16
+MF_FLAG_DEPTH_ALIGN = 32
 MF_NORM_COUNT, MF_NORM_MAX = 0, 1
 (MF_OK, MF_ERR_INVALID_ARG, MF_ERR_INVALID_POSE, MF_ERR_OOM, MF_ERR_NOT_READY,
  MF_ERR_TIMEOUT, MF_ERR_CUDA, MF_ERR_ADMISSION, MF_ERR_NO_DEVICE) = range(9)
@@ -108,7 +109,7 @@ FRAME_INFO_DTYPE = np.dtype([
     ("frame_index", "<i8"), ("status", "<i4"), ("n_valid", "<i4"), ("valid_mask", "<u4"),
     ("focus_valid", "<i4"), ("focus_u", "<f8"), ("focus_v", "<f8"), ("focus_px_x", "<i4"),
     ("focus_px_y", "<i4"), ("argmax_x", "<i4"), ("argmax_y", "<i4"), ("map_max", "<f4"),
-    ("reserved", "<i4")])
+    ("depth_scale", "<f4")])
 MOTION_POINT_DTYPE = np.dtype([("u", "<f8"), ("v", "<f8"), ("sigma", "<f8"), ("s", "<f8"),
                                ("valid", "<i4"), ("reserved", "<i4")])
 PUSH_DTYPE = np.dtype([("slot", "<i4"), ("n", "<i4"), ("poses", "<u8"), ("depth", "<u8"),

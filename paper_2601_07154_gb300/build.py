@@ -16,7 +16,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["mf_map_kernel.cu", "mf_map_tc.cu", "mf_pose_kernels.cu", "mf_stream.cpp", "mf_noalloc.cu",
-           "mf_engine.cpp", "mf_engine_kernels.cu", "mf_server.cpp", "mf_probe.cpp", "mf_fault.cpp"]
+           "mf_engine.cpp", "mf_engine_kernels.cu", "mf_server.cpp", "mf_probe.cpp", "mf_fault.cpp", "mf_align.cu"]
 
 
 def _nvcc():

@@ -377,6 +377,8 @@ void fill_slot_params(const Slot& s, const double* w, SlotParams* out) {
   out->fp.s_lo = s.d.s_lo;
   out->fp.s_hi = s.d.s_hi;
   out->d0 = (float)s.d.depth_ref_m;
+  out->fp.d0 = out->d0;
+  out->fp.depth_scale = 1.0f;
   for (int k = 0; k < mf::kMaxHist; ++k) out->w[k] = k < s.d.smooth_len ? w[k] : 0.0;
 }
 
@@ -634,6 +636,8 @@ int mf_engine_add_stream(mf_engine* e, const mf_stream_desc* d, int64_t reserve_
       free_slot = i;
       break;
     }
+  if (d->flags & MF_FLAG_DEPTH_ALIGN)
+    return fail(MF_ERR_INVALID_ARG, "depth alignment runs on mf_stream only, not in the engine");
   if (free_slot < 0) return fail(MF_ERR_ADMISSION, "every stream slot is taken");
   if (mf::fault_fires(mf::kFaultAdmissionFull))
     return fail(MF_ERR_ADMISSION, "admission refused (injected fault)");
@@ -790,6 +794,7 @@ int mf_engine_submit_batch(mf_engine* e, int32_t n, const mf_push* pushes, int32
 }
 
 int mf_engine_tick(mf_engine* e, int64_t* tick) {
+  mf::NvtxRange range("mf_engine_tick");
   if (!e || !tick) return fail(MF_ERR_INVALID_ARG, "NULL argument");
   *tick = -1;
   if (e->frames.empty()) return MF_OK;

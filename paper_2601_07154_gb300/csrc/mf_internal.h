@@ -6,6 +6,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/mf.h"
 #include "mf_ptr_kind.h"
 
@@ -42,7 +44,9 @@ struct alignas(16) FrameRec {
   int64_t frame_index;
   unsigned long long argmax_key;  // (bits of M << 32) | ~(y*W+x), max-reduced
   double focus_u, focus_v;
-  int32_t focus_valid, focus_px_x, focus_px_y, pad0;
+  int32_t focus_valid, focus_px_x, focus_px_y;
+  float d0;                    // reference depth of G, in this frame's depth scale
+  float depth_scale;           // the batch's depth alignment scale (reported)
   // slot-ordered FP64 records (slot s <-> frame n - W + 1 + s)
   double u[kMaxPts], v[kMaxPts], sigma[kMaxPts], s[kMaxPts];
   int32_t valid[kMaxPts];
@@ -57,6 +61,9 @@ struct IngestParams {
   int32_t* ring_bad;
   int64_t ring_mask;
   int64_t e0;              // global index of the first emitted frame
+  // Depth alignment: the push's batch scale (device; NULL = 1), applied to
+  // every translation of the push before anchoring.
+  const double* scale;
 };
 
 struct PointsParams {
@@ -72,6 +79,8 @@ struct PointsParams {
   double K[4];             // fx, fy, cx, cy at the calibration resolution
   double sigma_rel, s_lo, s_hi;
   double w[kMaxHist];      // least-squares weights, w[k] multiplies q_{i-k}
+  double d0;               // reference depth of the motion-guided depth (m)
+  const double* scale;     // the push's batch depth scale (device; NULL = 1)
 };
 
 struct MapParams {
@@ -84,7 +93,6 @@ struct MapParams {
   const void* depth;       // plane of frame f0, frames contiguous; may be NULL
   void* M;                 // plane of frame f0 (may be NULL)
   void* G;                 // (may be NULL)
-  float d0;
   int path;                // kMapAuto, kMapCudaCores or kMapTensorCores
   // Work counter of the persistent map kernels' dynamic unit schedule: 0 at
   // launch and left at 0; no two launches in flight may share it.
@@ -139,6 +147,23 @@ cudaError_t launch_map_tc(const MapParams& p, int window, int depth_dtype, int m
 cudaError_t launch_map(const MapParams& p, int window, int in_dtype, int out_dtype, int normalize,
                        cudaStream_t st, int64_t* launches);
 cudaError_t launch_finalize(const FinalizeParams& p, cudaStream_t st, int64_t* launches);
+
+// Depth alignment of one batch against the previous one (Section 2.2,
+// Fig. 3; mf_align.cu): *scale *= the lower median of the single-precision
+// ratios prev / cur over the `count` pixels where both depths are finite and
+// > 0 (unchanged when none qualifies).  Radix selection over the ratios'
+// bit patterns in three histogram passes; `work` holds kAlignWorkWords
+// words, and the launches leave nothing in it that the next call needs.
+constexpr int kAlignBins = 2048;
+constexpr int kAlignWorkWords = 3 * kAlignBins + 8;
+struct AlignParams {
+  const void* prev;        // previous batch's last overlap planes
+  const void* cur;         // this batch's first overlap planes
+  int64_t count;           // pixels compared (overlap frames x plane)
+  unsigned int* work;      // kAlignWorkWords words (zeroed by the launcher)
+  double* scale;           // batch scale, updated in place
+};
+cudaError_t launch_depth_align(const AlignParams& p, int depth_dtype, cudaStream_t st, int64_t* launches);
 cudaError_t launch_normalize(const NormalizeParams& p, int map_dtype, cudaStream_t st,
                              int64_t* launches);
 cudaError_t launch_ring_copy(const double* src, const int32_t* src_bad, int64_t src_mask,
@@ -147,6 +172,16 @@ cudaError_t launch_ring_copy(const double* src, const int32_t* src_bad, int64_t 
 
 // Map-kernel tile height used by the plain path.
 int map_tile_h(int width, int height, int window);
+
+// An NVTX range over one host call (push, get, tick, render): the timeline
+// of a profiler shows the path's calls around their kernels.  Costs a
+// function-pointer test when no tool is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Host helpers defined in mf_stream.cpp.
 bool host_ls_weights(int K, int mode, double* w);

@@ -216,10 +216,10 @@ __global__ void __launch_bounds__(kMapThreads) map_kernel(MapParams p) {
     if (p.G) {
       float4 g;
       if (has_depth) {
-        g.x = m.x * depth_weight(dv.x, p.d0);
-        g.y = m.y * depth_weight(dv.y, p.d0);
-        g.z = m.z * depth_weight(dv.z, p.d0);
-        g.w = m.w * depth_weight(dv.w, p.d0);
+        g.x = m.x * depth_weight(dv.x, rec->d0);
+        g.y = m.y * depth_weight(dv.y, rec->d0);
+        g.z = m.z * depth_weight(dv.z, rec->d0);
+        g.w = m.w * depth_weight(dv.w, rec->d0);
       } else {
         g = make_float4(0.f, 0.f, 0.f, 0.f);
       }
@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(kMapThreads, unit_ctas_per_sm(NMAX, CPT))
     ug.y0 = b * band_h;
     ug.rows = min(band_h, p.height - ug.y0);
     ug.gx0 = g * kGroupW;
-    ug.d0 = p.d0;
+    ug.d0 = ug.rec->d0;
     map_unit<NMAX, CPT, TIn, TOut, MODE>(ug, Ey, my_ring, P, s_kept, zeros);
     u = next_unit(p.sched, claim, units, s_next, k);
   }

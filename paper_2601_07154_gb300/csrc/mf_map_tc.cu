@@ -385,7 +385,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) map_tc_kernel(MapParams p, int 
           if (mplane) Scalar<TOut>::store(mplane, off, m);
           if (gplane) {
             const float dv = want_depth ? to_float(dtile[(r0 + j) * kTcCols + 32 * q + lane]) : 0.0f;
-            Scalar<TOut>::store(gplane, off, m * depth_weight(dv, p.d0));
+            Scalar<TOut>::store(gplane, off, m * depth_weight(dv, rec->d0));
           }
           cmax = fmaxf(cmax, m);
         }

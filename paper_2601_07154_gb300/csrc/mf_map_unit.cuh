@@ -29,6 +29,8 @@
 #include <cuda_fp16.h>
 #include <math.h>
 
+#include <type_traits>
+
 #include "mf_internal.h"
 
 namespace mf {
@@ -98,6 +100,22 @@ __device__ __forceinline__ float2 ffma2(float2 a, float b, float2 c) {
       : "=f"(d.x), "=f"(d.y)
       : "f"(a.x), "f"(a.y), "f"(b), "f"(c.x), "f"(c.y));
   return d;
+}
+
+// max(a, b, c) in one instruction (three-input max.f32 of sm_100 and later).
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+  float d;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+
+// Largest of one lane's CPT pixels of rows a and b (b only when `two`).
+template <int CPT>
+__device__ __forceinline__ float lane_max(const float2 (&a)[CPT / 2], const float2 (&b)[CPT / 2], bool two) {
+  float m = fmax3(a[0].x, a[0].y, two ? fmaxf(b[0].x, b[0].y) : a[0].x);
+#pragma unroll
+  for (int c = 1; c < CPT / 2; ++c) m = fmax3(m, fmaxf(a[c].x, a[c].y), two ? fmaxf(b[c].x, b[c].y) : m);
+  return m;
 }
 
 // min(1, d0 / D) for finite D > 0, else 0, without a compare or select:
@@ -447,8 +465,11 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
     return;
   }
 
+  // The lane's running maximum and the first row pair that holds it; the
+  // pixel is found once per unit after the rows (ties: lower row, then
+  // lower column, i.e. the lowest linear index).
   float best = -1.0f;
-  unsigned bidx = 0;
+  int brow = -1;
   // output rows advance by a stride: no per-row 64-bit multiply
   char* mrow = (MODE != kUnitMaxOnly && ug.M) ? ug.M + row0 * sizeof(TOut) : nullptr;
   char* grow = (MODE != kUnitMaxOnly && ug.G) ? ug.G + row0 * sizeof(TOut) : nullptr;
@@ -463,38 +484,86 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
     inv = scale ? 1.0f / mx : 1.0f;
   }
   const size_t ostride = (size_t)ug.width * sizeof(TOut);
-  auto emit = [&](const float2 (&acc)[CPT / 2], const float (&dv)[CPT], int r, size_t off) {
-    float m[CPT];
+  auto sums = [&](int r, bool two, float2 (&a)[CPT / 2], float2 (&b)[CPT / 2]) {
 #pragma unroll
-    for (int c = 0; c < CPT / 2; ++c) {
-      m[2 * c] = acc[c].x;
-      m[2 * c + 1] = acc[c].y;
-    }
-    if (MODE == kUnitScaled && scale) {
+    for (int c = 0; c < CPT / 2; ++c) a[c] = b[c] = make_float2(0.f, 0.f);
+    const float* ey0 = Ey + r * NMAX;
+    const float* ey1 = Ey + (two ? r + 1 : r) * NMAX;
+    if (nc == NMAX)
+      accum_two_rows<NMAX, CPT, NMAX>(ex, ey0, ey1, nc, a, b);
+    else
+      accum_two_rows<NMAX, CPT, 0>(ex, ey0, ey1, nc, a, b);
+  };
+  // Rows r and r+1 per iteration: the ring slots of rows r-2 and r-1 were
+  // consumed by the previous iteration, so rows r+S-2 and r+S-1 can be
+  // requested before rows r, r+1 are read.  FULL: depth, M and G all
+  // present (the common case), so the loop carries no per-row null checks.
+  auto rows_loop = [&](auto full_tag) {
+    constexpr bool FULL = decltype(full_tag)::value;
+    size_t off = 0;
+    for (int r = 0; r < rows; r += 2, off += 2 * ostride) {
+      issue(r + S - 2);
+      issue(r + S - 1);
+      cp_async_wait<S - 2>();
+      const bool two = r + 1 < rows;
+      float d0v[CPT], d1v[CPT];
 #pragma unroll
-      for (int c = 0; c < CPT; ++c) m[c] = m[c] == mx ? 1.0f : m[c] * inv;
-    }
-    if (mrow) Vec<TOut, CPT>::store(mrow + off, 0, m);
-    if (grow) {
-      float gv[CPT];
+      for (int c = 0; c < CPT; ++c) d0v[c] = d1v[c] = 0.0f;
+      if (FULL || dsrc) {
+        Vec<TIn, CPT>::unpack(ring_row<kInBytes>(my_ring, (r & (S - 1)) * 32 + lane), d0v);
+        if (two) Vec<TIn, CPT>::unpack(ring_row<kInBytes>(my_ring, ((r + 1) & (S - 1)) * 32 + lane), d1v);
+      }
+      float2 a[CPT / 2], b[CPT / 2];
+      sums(r, two, a, b);
+      if (!col_ok) continue;
+      if (MODE != kUnitMaxOnly) {
+        auto emit = [&](const float2 (&acc)[CPT / 2], const float (&dv)[CPT], size_t o) {
+          float m[CPT];
 #pragma unroll
-      for (int c = 0; c < CPT; ++c) gv[c] = m[c] * depth_weight(dv[c], ug.d0);
-      Vec<TOut, CPT>::store(grow + off, 0, gv);
+          for (int c = 0; c < CPT / 2; ++c) {
+            m[2 * c] = acc[c].x;
+            m[2 * c + 1] = acc[c].y;
+          }
+          if (MODE == kUnitScaled && scale) {
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) m[c] = m[c] == mx ? 1.0f : m[c] * inv;
+          }
+          if (FULL || mrow) Vec<TOut, CPT>::store(mrow + o, 0, m);
+          if (FULL || grow) {
+            float gv[CPT];
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) gv[c] = m[c] * depth_weight(dv[c], ug.d0);
+            Vec<TOut, CPT>::store(grow + o, 0, gv);
+          }
+        };
+        emit(a, d0v, off);
+        if (two) emit(b, d1v, off + ostride);
+      }
+      if (MODE != kUnitScaled) {
+        const float mm = lane_max<CPT>(a, b, two);
+        if (mm > best) {
+          best = mm;
+          brow = r;
+        }
+      }
     }
   };
-  // Running maximum of this lane's pixels, one compare per row pair; ties go
-  // to the lower row, then to the lower column (the lowest linear index).
-  auto track = [&](const float2 (&a)[CPT / 2], const float2 (&b)[CPT / 2], bool two, int r) {
-    float ma = fmaxf(a[0].x, a[0].y), mb = fmaxf(b[0].x, b[0].y);
+  if (dsrc && mrow && grow)
+    rows_loop(std::true_type{});
+  else
+    rows_loop(std::false_type{});
+  cp_async_wait<0>();
+  if (MODE != kUnitScaled) {
+    unsigned long long key = 0ull;
+    if (best >= 0.0f) {
+      // the winning row pair again, with the same sums in the same order
+      const bool two = brow + 1 < rows;
+      float2 a[CPT / 2], b[CPT / 2];
+      sums(brow, two, a, b);
+      float ma = fmaxf(a[0].x, a[0].y);
 #pragma unroll
-    for (int c = 1; c < CPT / 2; ++c) {
-      ma = fmaxf(ma, fmaxf(a[c].x, a[c].y));
-      mb = fmaxf(mb, fmaxf(b[c].x, b[c].y));
-    }
-    const float mm = two ? fmaxf(ma, mb) : ma;
-    if (mm > best) {
-      best = mm;
-      const bool first = ma == mm;
+      for (int c = 1; c < CPT / 2; ++c) ma = fmax3(ma, a[c].x, a[c].y);
+      const bool first = ma == best;
       float m[CPT];
 #pragma unroll
       for (int c = 0; c < CPT / 2; ++c) {
@@ -504,46 +573,12 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
       unsigned off = CPT - 1;
 #pragma unroll
       for (int c = CPT - 2; c >= 0; --c)
-        if (m[c] == mm) off = c;
-      bidx = (unsigned)((y0 + r + (first ? 0 : 1)) * ug.width + xc) + off;
+        if (m[c] == best) off = c;
+      const unsigned bidx = (unsigned)((y0 + brow + (first ? 0 : 1)) * ug.width + xc) + off;
+      key = ((unsigned long long)__float_as_uint(best) << 32) | (0xffffffffu - bidx);
     }
-  };
-  // Rows r and r+1 per iteration: the ring slots of rows r-2 and r-1 were
-  // consumed by the previous iteration, so rows r+S-2 and r+S-1
-  // can be requested before rows r, r+1 are read.
-  size_t off = 0;
-  for (int r = 0; r < rows; r += 2, off += 2 * ostride) {
-    issue(r + S - 2);
-    issue(r + S - 1);
-    cp_async_wait<S - 2>();
-    const bool two = r + 1 < rows;
-    float d0v[CPT], d1v[CPT];
-#pragma unroll
-    for (int c = 0; c < CPT; ++c) d0v[c] = d1v[c] = 0.0f;
-    if (dsrc) {
-      Vec<TIn, CPT>::unpack(ring_row<kInBytes>(my_ring, (r & (S - 1)) * 32 + lane), d0v);
-      if (two) Vec<TIn, CPT>::unpack(ring_row<kInBytes>(my_ring, ((r + 1) & (S - 1)) * 32 + lane), d1v);
-    }
-    float2 a[CPT / 2], b[CPT / 2];
-#pragma unroll
-    for (int c = 0; c < CPT / 2; ++c) a[c] = b[c] = make_float2(0.f, 0.f);
-    const float* ey0 = Ey + r * NMAX;
-    const float* ey1 = Ey + (two ? r + 1 : r) * NMAX;
-    if (nc == NMAX)
-      accum_two_rows<NMAX, CPT, NMAX>(ex, ey0, ey1, nc, a, b);
-    else
-      accum_two_rows<NMAX, CPT, 0>(ex, ey0, ey1, nc, a, b);
-    if (!col_ok) continue;
-    if (MODE != kUnitMaxOnly) {
-      emit(a, d0v, r, off);
-      if (two) emit(b, d1v, r + 1, off + ostride);
-    }
-    if (MODE != kUnitScaled) track(a, b, two, r);
+    publish_key(rec, key, n > 0);
   }
-  cp_async_wait<0>();
-  if (MODE != kUnitScaled)
-    publish_key(rec, best >= 0.0f ? ((unsigned long long)__float_as_uint(best) << 32) | (0xffffffffu - bidx) : 0ull,
-                n > 0);
 }
 
 // Dynamic shared memory of a CTA running units of bucket NMAX with CPT

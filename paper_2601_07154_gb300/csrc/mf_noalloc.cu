@@ -67,6 +67,7 @@ extern "C" int mf_render_noalloc(const mf_stream_desc* d, int32_t n_poses,
                                  const double* poses_w2c_3x4, int32_t n_render,
                                  const void* depth, const double* K, void* focus_map,
                                  void* guided_depth, mf_frame_info* info) {
+  mf::NvtxRange range("mf_render_noalloc");
   int rc = mf::host_validate_desc(d);
   if (rc) return rc;
   if (d->pose_frame != MF_POSES_WORLD)
@@ -144,6 +145,7 @@ extern "C" int mf_render_noalloc(const mf_stream_desc* d, int32_t n_poses,
     pp.s_lo = d->s_lo;
     pp.s_hi = d->s_hi;
     std::memcpy(pp.w, w, sizeof(pp.w));
+    pp.d0 = d->depth_ref_m;
     e = mf::launch_points(pp, st, &launches);
   }
   if (e == cudaSuccess) {
@@ -160,7 +162,6 @@ extern "C" int mf_render_noalloc(const mf_stream_desc* d, int32_t n_poses,
     mp.depth = depth;
     mp.M = focus_map;
     mp.G = guided_depth;
-    mp.d0 = (float)d->depth_ref_m;
     mp.path = mf::host_map_path(d->flags);
     mp.sched = sched;
     mp.fault = reinterpret_cast<unsigned int*>(scratch + kFaultOff);

@@ -62,17 +62,23 @@ __device__ __forceinline__ void split_coord(double u, float& hi, float& lo) {
 // the world y (gravity) axis closest to it, psi = atan2(R02 - R20, R00 + R22)
 // (pitch and roll are not propagated), with the translation that puts the
 // anchor's camera centre on its world position; T = L H^{-1}.
+//
+// scale: the batch's depth scale (depth alignment), multiplying every
+// translation of the batch before anchoring (1: the poses as given).
 __device__ __forceinline__ void ingest_frame(const double* in, int first, int k, int anchor,
                                              double* ring, int32_t* ring_bad, int64_t ring_mask,
-                                             int64_t e0) {
-  const double* L = in + (size_t)(first + k) * 12;
+                                             int64_t e0, double scale = 1.0) {
+  double L[12], La[12];
+  for (int e = 0; e < 12; ++e) L[e] = in[(size_t)(first + k) * 12 + e];
+  for (int r = 0; r < 3; ++r) L[4 * r + 3] *= scale;
   double out[12];
   for (int e = 0; e < 12; ++e) out[e] = L[e];
   bool bad = !pose_is_rigid(L);
   if (anchor) {
     const int64_t aslot = (e0 - 1) & ring_mask;
     const double* Ta = ring + aslot * 12;
-    const double* La = in + (size_t)(first - 1) * 12;
+    for (int e = 0; e < 12; ++e) La[e] = in[(size_t)(first - 1) * 12 + e];
+    for (int r = 0; r < 3; ++r) La[4 * r + 3] *= scale;
     if (ring_bad[aslot] || !pose_is_rigid(La)) {
       bad = true;
     } else {
@@ -120,6 +126,8 @@ struct FrameParams {
   int window, smooth_len;
   int width, height, calib_width, calib_height;
   double sigma_rel, s_lo, s_hi;
+  float d0;                // reference depth of G in the frame's depth scale
+  float depth_scale;       // the batch's depth alignment scale (reported only)
 };
 
 // Eqs. 1-6 for emitted frame g of a stream, by one warp (all 32 lanes).
@@ -265,6 +273,8 @@ __device__ __forceinline__ void frame_points(const double* ring, const int32_t* 
     rec->status = frame_bad ? MF_FRAME_BAD_POSE : (nv ? MF_FRAME_OK : MF_FRAME_EMPTY);
     rec->frame_index = g;
     rec->argmax_key = 0ull;
+    rec->d0 = fp.d0;
+    rec->depth_scale = fp.depth_scale;
   }
 }
 
@@ -304,7 +314,7 @@ __device__ __forceinline__ void finalize_frame(const FrameRec* rec, int width, m
     o.argmax_y = -1;
     o.map_max = 0.0f;
   }
-  o.reserved = 0;
+  o.depth_scale = rec->depth_scale;
   *out = o;
 }
 

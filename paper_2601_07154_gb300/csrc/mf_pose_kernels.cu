@@ -10,7 +10,8 @@ namespace mf {
 __global__ void __launch_bounds__(128) ingest_kernel(IngestParams p) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= p.n - p.first) return;
-  ingest_frame(p.in, p.first, k, p.anchor, p.ring, p.ring_bad, p.ring_mask, p.e0);
+  ingest_frame(p.in, p.first, k, p.anchor, p.ring, p.ring_bad, p.ring_mask, p.e0,
+               p.scale ? *p.scale : 1.0);
 }
 
 constexpr int kPtsWarps = 4;
@@ -31,6 +32,10 @@ __global__ void __launch_bounds__(kPtsWarps * 32) points_kernel(PointsParams p) 
   fp.sigma_rel = p.sigma_rel;
   fp.s_lo = p.s_lo;
   fp.s_hi = p.s_hi;
+  // G's reference depth in the frame's depth scale: min(1, d0 / (s D)) =
+  // min(1, (d0 / s) / D)
+  fp.d0 = (float)(p.scale ? p.d0 / *p.scale : p.d0);
+  fp.depth_scale = (float)(p.scale ? *p.scale : 1.0);
   frame_points(p.ring, p.ring_bad, p.ring_mask, g, fp, p.K, p.w, p.recs + (g & p.rec_mask), S[wi]);
 }
 

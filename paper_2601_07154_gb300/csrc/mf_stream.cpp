@@ -45,6 +45,9 @@ int fail(int status, const char* what, cudaError_t e = cudaSuccess) {
 
 size_t dtype_size(int dt) { return dt == MF_F32 ? 4 : 2; }
 
+// The first batch's depth scale (static storage: read by asynchronous copies).
+const double kUnitScale = 1.0;
+
 int map_path(uint32_t flags) {
   if (flags & MF_FLAG_MAP_TENSOR_CORES) return mf::kMapTensorCores;
   if (flags & MF_FLAG_MAP_CUDA_CORES) return mf::kMapCudaCores;
@@ -210,6 +213,17 @@ struct mf_stream {
   // device wait runs out sets it; the next completed wait reports it.
   unsigned int* fault_host = nullptr;
   unsigned int* fault_dev = nullptr;
+
+  // Depth alignment across batches (MF_FLAG_DEPTH_ALIGN): the batch scale
+  // (device double), the selection's work words, the previous batch's last
+  // `overlap` depth planes and, for host depth, an upload of this batch's
+  // first ones.
+  bool align = false;
+  double* scale_dev = nullptr;
+  unsigned int* align_work = nullptr;
+  char* ovl_prev = nullptr;
+  char* ovl_cur = nullptr;
+  bool ovl_valid = false;
 
   double* pose_dev = nullptr;      // device staging of host poses
   int64_t pose_dev_cap = 0;
@@ -452,6 +466,10 @@ void destroy(mf_stream* s) {
   s->dfree(s->ring_bad, (size_t)s->ring_cap * sizeof(int32_t));
   s->dfree(s->recs, (size_t)s->rec_cap * sizeof(FrameRec));
   s->dfree(s->sched, sizeof(unsigned int));
+  s->dfree(s->scale_dev, sizeof(double));
+  s->dfree(s->align_work, mf::kAlignWorkWords * sizeof(unsigned int));
+  s->dfree(s->ovl_prev, (size_t)s->d.overlap * s->plane_in);
+  s->dfree(s->ovl_cur, (size_t)s->d.overlap * s->plane_in);
   s->dfree(s->pose_dev, (size_t)s->pose_dev_cap * 12 * sizeof(double));
   s->dfree(s->stage, (size_t)s->stage_slots * s->plane_in);
   s->dfree(s->out_stage, s->out_stage_bytes);
@@ -495,6 +513,8 @@ int validate_desc(const mf_stream_desc* d) {
     return fail(MF_ERR_INVALID_ARG, "unknown normalisation");
   if ((d->flags & MF_FLAG_MAP_CUDA_CORES) && (d->flags & MF_FLAG_MAP_TENSOR_CORES))
     return fail(MF_ERR_INVALID_ARG, "choose one map kernel");
+  if ((d->flags & MF_FLAG_DEPTH_ALIGN) && d->pose_frame != MF_POSES_BATCH_LOCAL)
+    return fail(MF_ERR_INVALID_ARG, "depth alignment needs batch-local poses");
   if (!(d->sigma_rel > 0.0) || !(d->s_lo > 0.0) || !(d->s_hi >= d->s_lo) ||
       !(d->depth_ref_m > 0.0) || !std::isfinite(d->sigma_rel) || !std::isfinite(d->s_hi) ||
       !std::isfinite(d->depth_ref_m))
@@ -611,6 +631,23 @@ int mf_open_stream(const mf_stream_desc* d, mf_stream** out) {
     return fail(MF_ERR_OOM, "fault word allocation failed");
   }
   *s->fault_host = 0u;
+  if (d->flags & MF_FLAG_DEPTH_ALIGN) {
+    s->align = true;
+    s->scale_dev = (double*)s->dalloc(sizeof(double));
+    s->align_work = (unsigned int*)s->dalloc(mf::kAlignWorkWords * sizeof(unsigned int));
+    s->ovl_prev = (char*)s->dalloc((size_t)d->overlap * s->plane_in);
+    s->ovl_cur = (char*)s->dalloc((size_t)d->overlap * s->plane_in);
+    if (!s->scale_dev || !s->align_work || !s->ovl_prev || !s->ovl_cur) {
+      destroy(s);
+      return fail(MF_ERR_OOM, "depth alignment buffers");
+    }
+    if (cudaMemcpyAsync(s->scale_dev, &kUnitScale, sizeof(double), cudaMemcpyHostToDevice, s->st) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      destroy(s);
+      return fail(MF_ERR_CUDA, "depth scale initialisation failed");
+    }
+  }
   // every map launch of the stream leaves its counter at 0 again
   if (cudaMemsetAsync(s->sched, 0, sizeof(unsigned int), s->st) != cudaSuccess) {
     cudaGetLastError();
@@ -628,6 +665,7 @@ int mf_open_stream(const mf_stream_desc* d, mf_stream** out) {
 
 int mf_push_frames(mf_stream* s, int32_t n, const double* poses, const void* depth,
                    const double* K) {
+  mf::NvtxRange range("mf_push_frames");
   if (!s) return fail(MF_ERR_INVALID_ARG, "NULL stream");
   if (n < 1 || !poses || !K) return fail(MF_ERR_INVALID_ARG, "n < 1 or NULL poses/K");
   const bool local = s->d.pose_frame == MF_POSES_BATCH_LOCAL;
@@ -720,7 +758,28 @@ int mf_push_frames(mf_stream* s, int32_t n, const double* poses, const void* dep
     new_runs.push_back(Run{s->emitted, n_emit, nullptr, 0, nullptr});
   }
 
+  // Depth alignment: this batch's scale from the overlap frames' depth ratios
+  // against the previous batch (Section 2.2), before any pose is anchored.
+  if (s->align && depth && n < s->d.overlap)
+    return fail(MF_ERR_INVALID_ARG, "depth alignment needs batches of at least `overlap` frames");
+  if (s->align && O > 0 && depth && s->ovl_valid) {
+    const void* cur = depth;
+    if (depth_kind != mf::kPtrDevice) {
+      MF_CUDA(cudaMemcpyAsync(s->ovl_cur, depth, (size_t)O * s->plane_in, cudaMemcpyHostToDevice, s->st),
+              "overlap depth upload");
+      cur = s->ovl_cur;
+    }
+    mf::AlignParams ap{};
+    ap.prev = s->ovl_prev;
+    ap.cur = cur;
+    ap.count = (int64_t)O * s->d.width * s->d.height;
+    ap.work = s->align_work;
+    ap.scale = s->scale_dev;
+    MF_CUDA(mf::launch_depth_align(ap, s->d.depth_dtype, s->st, &s->launches), "depth alignment launch");
+  }
+
   mf::IngestParams ip{};
+  ip.scale = s->align ? s->scale_dev : nullptr;
   ip.in = pdev;
   ip.n = n;
   ip.first = O;
@@ -750,7 +809,24 @@ int mf_push_frames(mf_stream* s, int32_t n, const double* poses, const void* dep
   pp.s_lo = s->d.s_lo;
   pp.s_hi = s->d.s_hi;
   for (int k = 0; k < mf::kMaxHist; ++k) pp.w[k] = k < s->d.smooth_len ? s->w[k] : 0.0;
+  pp.d0 = s->d.depth_ref_m;
+  pp.scale = s->align ? s->scale_dev : nullptr;
   MF_CUDA(mf::launch_points(pp, s->st, &s->launches), "points launch");
+
+  // the last `overlap` depth planes, for the next batch's alignment (after
+  // the selection above has read the previous ones)
+  if (s->align) {
+    s->ovl_valid = depth != nullptr;
+    if (depth) {
+      const size_t bytes = (size_t)s->d.overlap * s->plane_in;
+      const char* src = static_cast<const char*>(depth) + (size_t)(n - s->d.overlap) * s->plane_in;
+      MF_CUDA(cudaMemcpyAsync(s->ovl_prev, src, bytes,
+                              depth_kind == mf::kPtrDevice ? cudaMemcpyDeviceToDevice
+                                                           : cudaMemcpyHostToDevice,
+                              s->st),
+              "overlap depth copy");
+    }
+  }
 
   for (const Run& r : new_runs) s->runs.push_back(r);
   s->emitted += n_emit;
@@ -762,6 +838,7 @@ int mf_push_frames(mf_stream* s, int32_t n, const double* poses, const void* dep
 int mf_get_maps(mf_stream* s, int32_t max_frames, void* focus_map, void* guided_depth,
                 mf_frame_info* info, mf_motion_point* points, int32_t* n_out,
                 int64_t timeout_ns) {
+  mf::NvtxRange range("mf_get_maps");
   if (!s || !n_out) return fail(MF_ERR_INVALID_ARG, "NULL stream or n_out");
   *n_out = 0;
   if (max_frames < 0) return fail(MF_ERR_INVALID_ARG, "max_frames < 0");
@@ -875,7 +952,6 @@ int mf_get_maps(mf_stream* s, int32_t max_frames, void* focus_map, void* guided_
     mp.depth = r.depth ? r.depth + (size_t)skip * s->plane_in : nullptr;
     mp.M = Mp;
     mp.G = Gp;
-    mp.d0 = (float)s->d.depth_ref_m;
     mp.path = map_path(s->d.flags);
     mp.sched = s->sched;
     mp.fault = s->fault_dev;
@@ -974,6 +1050,12 @@ int mf_reset_stream(mf_stream* s) {
     if (r.ready) s->free_events.push_back(r.ready);
   s->runs.clear();
   s->stage_head = s->stage_used = 0;
+  if (s->align) {  // the next batch is a first batch again: scale 1
+    DeviceGuard guard(s->device);
+    s->ovl_valid = false;
+    MF_CUDA(cudaMemcpyAsync(s->scale_dev, &kUnitScale, sizeof(double), cudaMemcpyHostToDevice, s->st),
+            "depth scale reset");
+  }
   return MF_OK;
 }
 

@@ -33,7 +33,8 @@ class MotionFocusStream:
                  pose_frame="world", overlap=0, depth_dtype=torch.float32,
                  map_dtype=torch.float32, calib=None, sigma_rel=0.1, s_lo=0.25, s_hi=4.0,
                  depth_ref_m=1.0, max_pending=1024, device=None, cuda_stream=None,
-                 time_kernels=False, torch_allocator=True, normalize="count", map_kernel="auto"):
+                 time_kernels=False, torch_allocator=True, normalize="count", map_kernel="auto",
+                 depth_align=False):
         self.device = torch.device(device) if device is not None else torch.device(
             "cuda", torch.cuda.current_device())
         self.width, self.height, self.window = int(width), int(height), int(window)
@@ -48,7 +49,8 @@ class MotionFocusStream:
                           overlap=int(overlap), depth_dtype=_DT[depth_dtype],
                           map_dtype=_DT[map_dtype], max_pending=int(max_pending),
                           flags=(_mf.MF_FLAG_TIME_KERNELS if time_kernels else 0)
-                          | _MAP_KERNELS[map_kernel],
+                          | _MAP_KERNELS[map_kernel]
+                          | (_mf.MF_FLAG_DEPTH_ALIGN if depth_align else 0),
                           normalize=_NORMS[normalize],
                           sigma_rel=sigma_rel, s_lo=s_lo, s_hi=s_hi, depth_ref_m=depth_ref_m,
                           # torch's default stream has handle 0, which the ABI
