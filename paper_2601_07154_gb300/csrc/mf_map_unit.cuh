@@ -102,6 +102,20 @@ __device__ __forceinline__ float2 ffma2(float2 a, float b, float2 c) {
   return d;
 }
 
+// a * b on both lanes of a (the first term of a sum: a product rounds
+// exactly as a fused multiply-add onto +0 does when the product is >= +0).
+__device__ __forceinline__ float2 fmul2(float2 a, float b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\t"
+      "mov.b64 rb, {%4, %4};\n\t"
+      "mul.rn.f32x2 rd, ra, rb;\n\t"
+      "mov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b));
+  return d;
+}
+
 // max(a, b, c) in one instruction (three-input max.f32 of sm_100 and later).
 __device__ __forceinline__ float fmax3(float a, float b, float c) {
   float d;
@@ -125,6 +139,22 @@ __device__ __forceinline__ float lane_max(const float2 (&a)[CPT / 2], const floa
 // gives 0 instead of saturating +inf to 1.
 __device__ __forceinline__ float depth_weight(float D, float d0) {
   return __saturatef(__fdividef(d0, D - 0x1p-149f));
+}
+
+// G = M min(1, d0 / D) for one lane's CPT pixels.
+template <int CPT>
+__device__ __forceinline__ void guided(const float (&m)[CPT], const float (&D)[CPT], float d0, float (&g)[CPT]) {
+#pragma unroll
+  for (int c = 0; c < CPT; c += 2) {
+    float x0, x1;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %4};\n\t"
+        "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(x0), "=f"(x1) : "f"(D[c]), "f"(D[c + 1]), "f"(-0x1p-149f));
+    const float w0 = __saturatef(__fdividef(d0, x0)), w1 = __saturatef(__fdividef(d0, x1));
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(g[c]), "=f"(g[c + 1]) : "f"(m[c]), "f"(m[c + 1]), "f"(w0), "f"(w1));
+  }
 }
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -243,8 +273,11 @@ template <int CPT>
 struct Vec<__half, CPT> : Vec16<__half, CPT> {};
 
 // Two rows' sums for one lane's CPT columns, points 0..nc-1 in order.  NC > 0
-// fixes the trip count at compile time (all NMAX points kept).
-template <int NMAX, int CPT, int NC>
+// fixes the trip count at compile time (all NMAX points kept).  INIT: the
+// sums start with the first point's product (nc >= 1; no zeroed
+// accumulators), else they add onto a and b as given.  Both give the same
+// bits: every term is >= +0.
+template <int NMAX, int CPT, int NC, bool INIT = false>
 __device__ __forceinline__ void accum_two_rows(const float2 (&ex)[NMAX][CPT / 2], const float* ey0,
                                                const float* ey1, int nc, float2 (&a)[CPT / 2],
                                                float2 (&b)[CPT / 2]) {
@@ -261,8 +294,13 @@ __device__ __forceinline__ void accum_two_rows(const float2 (&ex)[NMAX][CPT / 2]
     for (int k = 0; k < 4; ++k) {
 #pragma unroll
       for (int c = 0; c < CPT / 2; ++c) {
-        a[c] = ffma2(ex[i + k][c], es[k], a[c]);
-        b[c] = ffma2(ex[i + k][c], fs[k], b[c]);
+        if (INIT && i == 0 && k == 0) {
+          a[c] = fmul2(ex[0][c], es[0]);
+          b[c] = fmul2(ex[0][c], fs[0]);
+        } else {
+          a[c] = ffma2(ex[i + k][c], es[k], a[c]);
+          b[c] = ffma2(ex[i + k][c], fs[k], b[c]);
+        }
       }
     }
   }
@@ -317,11 +355,19 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
   const char* dsrc = (MODE != kUnitMaxOnly && ug.depth) ? ug.depth + row0 * sizeof(TIn) : nullptr;
   const size_t dstride = (size_t)ug.width * sizeof(TIn);
   static_assert((S & (S - 1)) == 0, "ring stages must be a power of two");
-  auto issue = [&](int r) {
-    if (r < rows && col_ok && dsrc)
-      cp_async<kInBytes>(reinterpret_cast<char*>(my_ring) + ((r & (S - 1)) * 32 + lane) * kInBytes,
-                         dsrc + (size_t)r * dstride);
+  // Depth rows are requested in order, one group per row: rq is the next
+  // row to request and dq its source (a running pointer, no per-row
+  // multiply).  `sure`: the caller knows that dsrc is set and the lane's
+  // columns lie inside the frame.
+  int rq = 0;
+  uintptr_t dq = reinterpret_cast<uintptr_t>(dsrc);
+  auto issue = [&](bool sure) {
+    if (rq < rows && (sure || (col_ok && dsrc)))
+      cp_async<kInBytes>(reinterpret_cast<char*>(my_ring) + ((rq & (S - 1)) * 32 + lane) * kInBytes,
+                         reinterpret_cast<const char*>(dq));
     cp_async_commit();
+    ++rq;
+    dq += dstride;
   };
   // The ring is this warp's own and the previous unit drained it.
   __syncthreads();  // the previous unit is done with P and Ey
@@ -436,7 +482,8 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
   if (strip_zero) dsrc = nullptr;
   // the first depth rows are in flight while the factors are computed
 #pragma unroll
-  for (int s = 0; s < S - 2; ++s) issue(s);
+  dq = reinterpret_cast<uintptr_t>(dsrc);  // after the strip test (dsrc may have been dropped)
+  for (int s = 0; s < S - 2; ++s) issue(false);
   const int nc = min(NMAX, (nk + 3) & ~3);
   for (int r = warp; r < rows; r += kMapThreads / 32)
     for (int i = lane; i < nc; i += 32)
@@ -470,7 +517,6 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
   // lower column, i.e. the lowest linear index).
   float best = -1.0f;
   int brow = -1;
-  // output rows advance by a stride: no per-row 64-bit multiply
   char* mrow = (MODE != kUnitMaxOnly && ug.M) ? ug.M + row0 * sizeof(TOut) : nullptr;
   char* grow = (MODE != kUnitMaxOnly && ug.G) ? ug.G + row0 * sizeof(TOut) : nullptr;
   // Scaled pass: divide by the maximum the first pass found (IEEE reciprocal
@@ -484,40 +530,46 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
     inv = scale ? 1.0f / mx : 1.0f;
   }
   const size_t ostride = (size_t)ug.width * sizeof(TOut);
+  // Sums of rows r and r+1 (r alone when !two): they start with the first
+  // point's product; no kept point (nc = 0) gives zeros.
   auto sums = [&](int r, bool two, float2 (&a)[CPT / 2], float2 (&b)[CPT / 2]) {
-#pragma unroll
-    for (int c = 0; c < CPT / 2; ++c) a[c] = b[c] = make_float2(0.f, 0.f);
     const float* ey0 = Ey + r * NMAX;
     const float* ey1 = Ey + (two ? r + 1 : r) * NMAX;
-    if (nc == NMAX)
-      accum_two_rows<NMAX, CPT, NMAX>(ex, ey0, ey1, nc, a, b);
-    else
-      accum_two_rows<NMAX, CPT, 0>(ex, ey0, ey1, nc, a, b);
+    if (nc == NMAX) {
+      accum_two_rows<NMAX, CPT, NMAX, true>(ex, ey0, ey1, nc, a, b);
+    } else if (nc > 0) {
+      accum_two_rows<NMAX, CPT, 0, true>(ex, ey0, ey1, nc, a, b);
+    } else {
+#pragma unroll
+      for (int c = 0; c < CPT / 2; ++c) a[c] = b[c] = make_float2(0.f, 0.f);
+    }
   };
-  // Rows r and r+1 per iteration: the ring slots of rows r-2 and r-1 were
-  // consumed by the previous iteration, so rows r+S-2 and r+S-1 can be
-  // requested before rows r, r+1 are read.  FULL: depth, M and G all
-  // present (the common case), so the loop carries no per-row null checks.
-  auto rows_loop = [&](auto full_tag) {
-    constexpr bool FULL = decltype(full_tag)::value;
-    size_t off = 0;
+  // Rows r and r+1 per step: the ring slots of rows r-2 and r-1 were
+  // consumed by the previous step, so rows r+S-2 and r+S-1 can be requested
+  // before rows r, r+1 are read.  FAST: depth, M and G all present, every
+  // lane's columns inside the frame and an even number of rows (the common
+  // case), so a step carries no null, column or last-row checks.
+  auto rows_loop = [&](auto fast_tag) {
+    constexpr bool FAST = decltype(fast_tag)::value;
+    size_t off = 0;  // output rows advance by a stride: no per-row 64-bit multiply
     for (int r = 0; r < rows; r += 2, off += 2 * ostride) {
-      issue(r + S - 2);
-      issue(r + S - 1);
+      const bool TWO = FAST || r + 1 < rows;
+      issue(FAST);
+      issue(FAST);
       cp_async_wait<S - 2>();
-      const bool two = r + 1 < rows;
       float d0v[CPT], d1v[CPT];
 #pragma unroll
       for (int c = 0; c < CPT; ++c) d0v[c] = d1v[c] = 0.0f;
-      if (FULL || dsrc) {
+      if (FAST || dsrc) {
         Vec<TIn, CPT>::unpack(ring_row<kInBytes>(my_ring, (r & (S - 1)) * 32 + lane), d0v);
-        if (two) Vec<TIn, CPT>::unpack(ring_row<kInBytes>(my_ring, ((r + 1) & (S - 1)) * 32 + lane), d1v);
+        if (TWO) Vec<TIn, CPT>::unpack(ring_row<kInBytes>(my_ring, ((r + 1) & (S - 1)) * 32 + lane), d1v);
       }
       float2 a[CPT / 2], b[CPT / 2];
-      sums(r, two, a, b);
-      if (!col_ok) continue;
+      sums(r, TWO, a, b);
+      if (!FAST && !col_ok) continue;
       if (MODE != kUnitMaxOnly) {
-        auto emit = [&](const float2 (&acc)[CPT / 2], const float (&dv)[CPT], size_t o) {
+        const size_t o = off;
+        auto emit = [&](const float2 (&acc)[CPT / 2], const float (&dv)[CPT], size_t oo) {
           float m[CPT];
 #pragma unroll
           for (int c = 0; c < CPT / 2; ++c) {
@@ -528,19 +580,18 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
 #pragma unroll
             for (int c = 0; c < CPT; ++c) m[c] = m[c] == mx ? 1.0f : m[c] * inv;
           }
-          if (FULL || mrow) Vec<TOut, CPT>::store(mrow + o, 0, m);
-          if (FULL || grow) {
+          if (FAST || mrow) Vec<TOut, CPT>::store(mrow + oo, 0, m);
+          if (FAST || grow) {
             float gv[CPT];
-#pragma unroll
-            for (int c = 0; c < CPT; ++c) gv[c] = m[c] * depth_weight(dv[c], ug.d0);
-            Vec<TOut, CPT>::store(grow + o, 0, gv);
+            guided<CPT>(m, dv, ug.d0, gv);
+            Vec<TOut, CPT>::store(grow + oo, 0, gv);
           }
         };
-        emit(a, d0v, off);
-        if (two) emit(b, d1v, off + ostride);
+        emit(a, d0v, o);
+        if (TWO) emit(b, d1v, o + ostride);
       }
       if (MODE != kUnitScaled) {
-        const float mm = lane_max<CPT>(a, b, two);
+        const float mm = lane_max<CPT>(a, b, TWO);
         if (mm > best) {
           best = mm;
           brow = r;
@@ -548,7 +599,8 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
       }
     }
   };
-  if (dsrc && mrow && grow)
+  const bool inside = x0 + kStrip <= ug.width;  // warp-uniform: every lane's columns
+  if (dsrc && mrow && grow && inside && (rows & 1) == 0)
     rows_loop(std::true_type{});
   else
     rows_loop(std::false_type{});
