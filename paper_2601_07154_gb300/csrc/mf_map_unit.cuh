@@ -132,14 +132,23 @@ __device__ __forceinline__ float lane_max(const float2 (&a)[CPT / 2], const floa
   return m;
 }
 
-// min(1, d0 / D) for finite D > 0, else 0, without a compare or select:
-// the saturated quotient is min(1, d0/D) for D > 0 and 0 for negative, NaN
-// and infinite D.  Subtracting the smallest denormal leaves every normal D
-// unchanged and moves D = +0 (and -0) below zero, so that "no depth" also
-// gives 0 instead of saturating +inf to 1.
-__device__ __forceinline__ float depth_weight(float D, float d0) {
-  return __saturatef(__fdividef(d0, D - 0x1p-149f));
+// min(1, d0 / x) for x = D - 2^-149, as one approximate reciprocal (PTX
+// rcp.approx.ftz, within about an ulp) and one saturating product, with no
+// compare or select.  Subtracting the smallest denormal leaves every normal
+// D unchanged and moves D = +0 and -0 below zero; the flush to zero of the
+// reciprocal's input then gives:
+//   normal D > 0        -> min(1, d0 / D);
+//   positive denormal D -> 1/x = +inf -> 1 (the clamp of a huge quotient);
+//   D = +-0, D < 0      -> 1/x <= -0 -> 0 ("no depth");
+//   D = NaN             -> NaN, which the saturation turns into 0;
+//   D = +inf            -> 0;  D = -inf -> -0 -> 0.
+__device__ __forceinline__ float weight_of(float x, float d0) {
+  float r, w;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  asm("mul.rn.sat.f32 %0, %1, %2;" : "=f"(w) : "f"(d0), "f"(r));
+  return w;
 }
+__device__ __forceinline__ float depth_weight(float D, float d0) { return weight_of(D - 0x1p-149f, d0); }
 
 // G = M min(1, d0 / D) for one lane's CPT pixels.
 template <int CPT>
@@ -150,7 +159,7 @@ __device__ __forceinline__ void guided(const float (&m)[CPT], const float (&D)[C
     asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %4};\n\t"
         "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
         : "=f"(x0), "=f"(x1) : "f"(D[c]), "f"(D[c + 1]), "f"(-0x1p-149f));
-    const float w0 = __saturatef(__fdividef(d0, x0)), w1 = __saturatef(__fdividef(d0, x1));
+    const float w0 = weight_of(x0, d0), w1 = weight_of(x1, d0);
     asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
         "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
         : "=f"(g[c]), "=f"(g[c + 1]) : "f"(m[c]), "f"(m[c + 1]), "f"(w0), "f"(w1));

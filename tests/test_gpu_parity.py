@@ -280,12 +280,20 @@ def test_bad_pose_and_invalid_depth(mf, kernel):
     depth[:, 2, :] = np.inf
     depth[:, 3, :] = -1.0
     depth[:, 4, :] = 0.5
+    depth[:, 5, :] = -np.inf
+    depth[:, 6, :] = -0.0
+    depth[:, 7, 0::2] = np.float32(2.0 ** -149)      # positive denormals: finite D > 0
+    depth[:, 7, 1::2] = np.float32(3.0 * 2.0 ** -140)
+    depth[:, 8, 0::2] = -np.float32(2.0 ** -149)     # negative denormals
+    depth[:, 8, 1::2] = np.float32(2.0 ** 127)       # near the top of the range
     K = np.array([50.0, 50.0, 32.0, 24.0])
     M, G, info, pts, ref = run_both(mf, poses, depth, K, 64, 48, window=4, smooth_len=3,
                                     map_kernel=kernel)
     compare_all(M, G, info, pts, ref, K)
     assert info["status"][12] == O.FRAME_BAD_POSE and info["valid_mask"][13] == 0b0011
     assert not G[:, :4].any() and np.array_equal(G[:, 4], M[:, 4])
+    assert not G[:, 5:7].any() and not G[:, 8, 0::2].any()
+    assert np.array_equal(G[:, 7], M[:, 7])          # min(1, d0 / D) = 1 for denormal D > 0
 
 
 def test_host_pointers_match_device_pointers(mf):
