@@ -951,10 +951,10 @@ class OraclePool:
 def cpu_baseline(w, seconds):
     pool = OraclePool()
     try:
-        # calibrate on one frame, then size the sample to ~`seconds`
-        cred, dt = pool.frames([450], HEIGHT)
-        nframes = max(1, min(900 - 451, int(seconds * cred / dt)))
-        frames = list(range(451, 451 + nframes))
+        # calibrate on one frame per worker, then size the sample to ~`seconds`
+        cred, dt = pool.frames(list(range(450 - pool.workers, 450)), HEIGHT)
+        nframes = max(1, min(900 - 450, int(seconds * cred / dt)))
+        frames = list(range(450, 450 + nframes))
         cred, dt = pool.frames(frames, HEIGHT)
     finally:
         pool.close()

@@ -427,12 +427,24 @@ template <typename TIn, typename TOut, bool VEC>
 cudaError_t launch_tc_typed(const MapParams& p, int kk_max, cudaStream_t st) {
   auto k = map_tc_kernel<TIn, TOut, VEC>;
   const size_t smem = tc_smem_bytes(kk_max, sizeof(TIn));
-  // resident CTAs per SM from the kernel's footprint (shared memory incl.
-  // the per-block reservation, registers) on this device, at most 4: each
-  // CTA holds 128 TMEM columns, and four fill an SM's 512
+  // Shared-memory opt-in and carveout on this device (cached per device);
+  // resident CTAs per SM from the kernel's own footprint -- shared memory
+  // with the per-block reservation, registers -- at the full carveout it
+  // asks for (the occupancy query does not assume that carveout), at most 4:
+  // each CTA holds 128 TMEM columns, and four fill an SM's 512.
   const KernelFit f = host_kernel_fit(reinterpret_cast<const void*>(k), kTcThreads,
                                       tc_smem_bytes(kTcKsMax, sizeof(TIn)), smem, 100);
-  const int per_sm = std::max(1, std::min(f.per_sm, 4));
+  int dev = 0, smem_sm = 0, reserved = 0, regs_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+  cudaFuncAttributes fa{};
+  cudaFuncGetAttributes(&fa, k);
+  const size_t per_cta = smem + fa.sharedSizeBytes + (size_t)reserved;
+  int fit = (int)((size_t)smem_sm / per_cta);
+  if (fa.numRegs > 0) fit = std::min(fit, regs_sm / (fa.numRegs * kTcThreads));
+  const int per_sm = std::max(1, std::min(fit, 4));
   const int sms = f.sms;
   const int strips = (p.width + kTcCols - 1) / kTcCols;
   const long long items = (long long)p.n_frames * strips;
