@@ -898,6 +898,8 @@ def _oracle_worker_init(accel):
     import oracle as O
     from synth import hd_stream
     w = hd_stream(accel=accel)
+    for k in range(w.ring):          # the depth ring is rendered before any timing
+        w.depth(k)
     ref = O.OracleStream(O.Params(WIDTH, HEIGHT, window=WINDOW, smooth_len=SMOOTH))
     ref.push(w.poses, None, w.K())
     _ORACLE.update(O=O, w=w, ref=ref)

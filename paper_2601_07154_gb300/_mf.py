@@ -12,7 +12,8 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libmf.so")
+# MF_CHECKED=1 loads the checked debug library (bounds-checked map kernels)
+LIB_PATH = os.path.join(_HERE, "libmf_checked.so" if os.environ.get("MF_CHECKED") == "1" else "libmf.so")
 
 MF_F32, MF_BF16, MF_F16 = 0, 1, 2
 MF_MODE_ACCEL, MF_MODE_HEADING = 0, 1

@@ -1,7 +1,11 @@
 """Builds libmf.so (CUDA kernels + C ABI) in-tree for sm_103a with nvcc.
 
 Translation units compile in parallel into ``_build/`` and link into
-``libmf.so`` beside this file.  A unit is rebuilt only when it or a header is
+``libmf.so`` beside this file.  ``build(checked=True)`` builds the checked
+debug library instead (``-DMF_CHECKED``: every global access of the map
+kernels is tested against its plane, and one outside is reported and
+skipped) into ``_build_checked/`` and ``libmf_checked.so``; the binding
+loads it when MF_CHECKED=1 is set.  A unit is rebuilt only when it or a header is
 newer than its object.  Host code uses no architecture-specific intrinsics,
 so the same sources build on x86_64 and aarch64 hosts.
 """
@@ -30,19 +34,22 @@ def _headers():
     return hs
 
 
-def build(verbose=False, force=False):
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose=False, force=False, checked=False):
+    build_dir = BUILD + "_checked" if checked else BUILD
+    lib = os.path.join(HERE, "libmf_checked.so") if checked else LIB
+    defs = ["-DMF_CHECKED"] if checked else []
+    os.makedirs(build_dir, exist_ok=True)
     nvcc = _nvcc()
     newest_header = max(os.path.getmtime(h) for h in _headers())
     procs, objs = [], []
     for src in SOURCES:
         path = os.path.join(CSRC, src)
-        obj = os.path.join(BUILD, src + ".o")
+        obj = os.path.join(build_dir, src + ".o")
         objs.append(obj)
         if (not force and os.path.exists(obj)
                 and os.path.getmtime(obj) >= max(os.path.getmtime(path), newest_header)):
             continue
-        cmd = [nvcc, *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
+        cmd = [nvcc, *ARCH, *defs, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
                "-I", os.path.join(ROOT, "include"), "-c", path, "-o", obj]
         if src.endswith(".cpp"):
             cmd[1:1] = ["-x", "cu"]
@@ -59,16 +66,16 @@ def build(verbose=False, force=False):
             sys.stdout.write(out.decode(errors="replace"))
     if failed:
         raise RuntimeError("nvcc failed for " + ", ".join(failed))
-    if procs or not os.path.exists(LIB):
+    if procs or not os.path.exists(lib):
         cuda_lib = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "lib64")
-        cmd = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", LIB + ".tmp", *objs,
+        cmd = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", lib + ".tmp", *objs,
                "-Xlinker", "-rpath," + cuda_lib]
         if verbose:
             print(" ".join(cmd), flush=True)
         subprocess.run(cmd, check=True)
-        os.replace(LIB + ".tmp", LIB)
-    return LIB
+        os.replace(lib + ".tmp", lib)
+    return lib
 
 
 if __name__ == "__main__":
-    build(verbose=True, force="--force" in sys.argv)
+    build(verbose=True, force="--force" in sys.argv, checked="--checked" in sys.argv)

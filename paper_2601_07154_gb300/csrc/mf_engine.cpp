@@ -260,6 +260,7 @@ mf::EngineKernelArgs kernel_args(mf_engine* e, int b) {
   a.recs = e->recs;
   a.max_frames = e->d.max_tick_frames;
   a.sched = e->sched;
+  a.fault = e->sched + mf::kEnginePaths;
   return a;
 }
 
@@ -309,7 +310,7 @@ void destroy(mf_engine* e) {
     if (e->t0[b]) cudaEventDestroy(e->t0[b]);
   }
   e->dfree(e->recs, (size_t)e->d.max_tick_frames * sizeof(FrameRec));
-  e->dfree(e->sched, mf::kEnginePaths * sizeof(unsigned int));
+  e->dfree(e->sched, (mf::kEnginePaths + 1) * sizeof(unsigned int));
   e->dfree(e->slots_dev, (size_t)(e->d.max_streams + 1) * sizeof(SlotParams));
   if (e->cap_st) cudaStreamDestroy(e->cap_st);
   if (e->fork.side) {
@@ -345,7 +346,14 @@ int wait_tick(mf_engine* e, int64_t t, int64_t timeout_ns) {
   if (t < 0 || t >= e->next_tick) return MF_OK;
   const int b = (int)(t & 1);
   if (e->buf_tick[b] != t) return MF_OK;  // buffer reused: tick t finished earlier
-  return wait_event(e->done[b], timeout_ns);
+  const int rc = wait_event(e->done[b], timeout_ns);
+  if (rc || !mf::kChecked) return rc;
+  // checked builds: an access outside a plane was caught and skipped
+  unsigned int f = 0u;
+  ENG_CUDA(cudaMemcpy(&f, e->sched + mf::kEnginePaths, sizeof(f), cudaMemcpyDeviceToHost), "fault word");
+  if (f == 0u) return MF_OK;
+  ENG_CUDA(cudaMemset(e->sched + mf::kEnginePaths, 0, sizeof(f)), "fault word");
+  return fail(MF_ERR_CUDA, "checked build: an index outside its plane was caught (access skipped)");
 }
 
 int collect_timers(mf_engine* e) {
@@ -570,11 +578,12 @@ int mf_engine_open(const mf_engine_desc* d, mf_engine** out) {
     e->slots_pinned = nullptr;
   }
   e->recs = (FrameRec*)e->dalloc((size_t)d->max_tick_frames * sizeof(FrameRec));
-  e->sched = (unsigned int*)e->dalloc(mf::kEnginePaths * sizeof(unsigned int));
+  // the map paths' work counters, then the fault word of checked builds
+  e->sched = (unsigned int*)e->dalloc((mf::kEnginePaths + 1) * sizeof(unsigned int));
   if (e->sched &&
-      cudaMemsetAsync(e->sched, 0, mf::kEnginePaths * sizeof(unsigned int), e->st) != cudaSuccess) {
+      cudaMemsetAsync(e->sched, 0, (mf::kEnginePaths + 1) * sizeof(unsigned int), e->st) != cudaSuccess) {
     cudaGetLastError();
-    e->dfree(e->sched, mf::kEnginePaths * sizeof(unsigned int));
+    e->dfree(e->sched, (mf::kEnginePaths + 1) * sizeof(unsigned int));
     e->sched = nullptr;
   }
   e->tab_bytes = table_bytes(d->max_tick_frames, d->max_streams, e->poses_cap());

@@ -83,6 +83,7 @@ struct EngineKernelArgs {
   // one work counter per map path for the dynamic unit schedule (0 between
   // launches; the two paths run concurrently, so each has its own)
   unsigned int* sched;         // [kEnginePaths]
+  unsigned int* fault;         // checked builds: set on an access outside a plane
 };
 
 // Kernel launches of one tick: ingest, points, the two map paths, finalize.

@@ -97,6 +97,7 @@ __global__ void __launch_bounds__(kMapThreads, unit_ctas_per_sm(NMAX, CPT)) engi
     ug.M = fr.M;
     ug.G = fr.G;
     ug.width = sp.fp.width;
+    ug.fault = a.fault;
     ug.height = sp.fp.height;
     ug.y0 = b * fr.band_h;
     ug.rows = min(fr.band_h, ug.height - ug.y0);

@@ -173,6 +173,20 @@ cudaError_t launch_ring_copy(const double* src, const int32_t* src_bad, int64_t 
 // Map-kernel tile height used by the plain path.
 int map_tile_h(int width, int height, int window);
 
+// Checked build (compiled with -DMF_CHECKED, libmf_checked.so): the map
+// kernels test every global access against its plane before making it.  An
+// access outside sets the launch's fault word to kFaultOutOfRange and is
+// skipped, so an index error is reported instead of faulting the GPU (a
+// stand-in for a memory checker where none can run).  Release builds test
+// nothing.
+constexpr unsigned int kFaultWaitExpired = 1u;
+constexpr unsigned int kFaultOutOfRange = 2u;
+#ifdef MF_CHECKED
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
+
 // An NVTX range over one host call (push, get, tick, render): the timeline
 // of a profiler shows the path's calls around their kernels.  Costs a
 // function-pointer test when no tool is attached.

@@ -284,6 +284,7 @@ __global__ void __launch_bounds__(kMapThreads, unit_ctas_per_sm(NMAX, CPT))
     ug.M = p.M ? static_cast<char*>(p.M) + (size_t)f * plane * sizeof(TOut) : nullptr;
     ug.G = p.G ? static_cast<char*>(p.G) + (size_t)f * plane * sizeof(TOut) : nullptr;
     ug.width = p.width;
+    ug.fault = p.fault;
     ug.height = p.height;
     ug.y0 = b * band_h;
     ug.rows = min(band_h, p.height - ug.y0);

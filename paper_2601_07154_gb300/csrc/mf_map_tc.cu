@@ -209,7 +209,7 @@ __device__ __forceinline__ void fetch_depth(TIn* sD, const TIn* dplane, int widt
 // NaN-filled bands silently.
 __device__ __forceinline__ void report_wait_expired(const MapParams& p, const FrameRec* rec) {
   atomicExch(reinterpret_cast<int*>(const_cast<int32_t*>(&rec->status)), (int)MF_FRAME_TIMEOUT);
-  if (p.fault) atomicExch_system(p.fault, 1u);
+  if (p.fault) atomicExch_system(p.fault, kFaultWaitExpired);
 }
 
 __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t phase) {

@@ -337,7 +337,18 @@ struct UnitGeom {
   int y0, rows;       // band
   int gx0;            // first column of the strip group
   float d0;
+  unsigned int* fault;  // checked builds: reports an access outside the planes (may be NULL)
 };
+
+// Checked builds: rows y of columns x .. x + n - 1 lie in the unit's
+// planes (else the fault word is set and the caller skips the access).
+// Release builds: always true, and the test compiles away.
+__device__ __forceinline__ bool in_plane(const UnitGeom& ug, int y, int x, int n) {
+  if (!kChecked) return true;
+  const bool ok = y >= 0 && y < ug.height && x >= 0 && n >= 0 && x + n <= ug.width;
+  if (!ok && ug.fault) atomicExch_system(ug.fault, kFaultOutOfRange);
+  return ok;
+}
 
 // What a pass over a unit produces.  Full: M, G and the frame's argmax.
 // MaxOnly: the argmax alone (no memory traffic), the first pass of
@@ -371,7 +382,7 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
   int rq = 0;
   uintptr_t dq = reinterpret_cast<uintptr_t>(dsrc);
   auto issue = [&](bool sure) {
-    if (rq < rows && (sure || (col_ok && dsrc)))
+    if (rq < rows && (sure || (col_ok && dsrc)) && in_plane(ug, y0 + rq, xc, CPT))
       cp_async<kInBytes>(reinterpret_cast<char*>(my_ring) + ((rq & (S - 1)) * 32 + lane) * kInBytes,
                          reinterpret_cast<const char*>(dq));
     cp_async_commit();
@@ -394,6 +405,7 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
         const size_t first = (size_t)y0 * ug.width + x0;
         for (int r = lane; r < rows; r += 32) {
           const size_t at = (first + (size_t)r * ug.width) * sizeof(TOut);
+          if (!in_plane(ug, y0 + r, x0, (int)(bytes / sizeof(TOut)))) continue;
           if (ug.M) bulk_copy_s2g(ug.M + at, zeros, bytes);
           if (ug.G) bulk_copy_s2g(ug.G + at, zeros, bytes);
         }
@@ -403,7 +415,9 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
         const size_t ostride = (size_t)ug.width * sizeof(TOut);
         char* qm = ug.M ? ug.M + row0 * sizeof(TOut) : nullptr;
         char* qg = ug.G ? ug.G + row0 * sizeof(TOut) : nullptr;
-        for (size_t off = 0, end = (size_t)rows * ostride; off < end; off += ostride) {
+        int ry = y0;
+        for (size_t off = 0, end = (size_t)rows * ostride; off < end; off += ostride, ++ry) {
+          if (!in_plane(ug, ry, xc, CPT)) continue;
           if (qm) Vec<TOut, CPT>::store(qm + off, 0, z);
           if (qg) Vec<TOut, CPT>::store(qg + off, 0, z);
         }
@@ -460,6 +474,7 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
       const size_t first = (size_t)y0 * ug.width + ug.gx0;
       for (int r = tid; r < rows; r += kMapThreads) {
         const size_t at = (first + (size_t)r * ug.width) * sizeof(TOut);
+        if (!in_plane(ug, y0 + r, ug.gx0, cols)) continue;
         if (ug.M) bulk_copy_s2g(ug.M + at, zeros, bytes);
         if (ug.G) bulk_copy_s2g(ug.G + at, zeros, bytes);
       }
@@ -578,7 +593,7 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
       if (!FAST && !col_ok) continue;
       if (MODE != kUnitMaxOnly) {
         const size_t o = off;
-        auto emit = [&](const float2 (&acc)[CPT / 2], const float (&dv)[CPT], size_t oo) {
+        auto emit = [&](const float2 (&acc)[CPT / 2], const float (&dv)[CPT], size_t oo, int ry) {
           float m[CPT];
 #pragma unroll
           for (int c = 0; c < CPT / 2; ++c) {
@@ -589,6 +604,7 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
 #pragma unroll
             for (int c = 0; c < CPT; ++c) m[c] = m[c] == mx ? 1.0f : m[c] * inv;
           }
+          if (!in_plane(ug, ry, xc, CPT)) return;
           if (FAST || mrow) Vec<TOut, CPT>::store(mrow + oo, 0, m);
           if (FAST || grow) {
             float gv[CPT];
@@ -596,8 +612,8 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
             Vec<TOut, CPT>::store(grow + oo, 0, gv);
           }
         };
-        emit(a, d0v, o);
-        if (TWO) emit(b, d1v, o + ostride);
+        emit(a, d0v, o, y0 + r);
+        if (TWO) emit(b, d1v, o + ostride, y0 + r + 1);
       }
       if (MODE != kUnitScaled) {
         const float mm = lane_max<CPT>(a, b, TWO);

@@ -396,7 +396,10 @@ int ensure_out_stage(mf_stream* s, size_t bytes) {
 // kernel since the last report (the fault word), or one injected on the host.
 int check_fault(mf_stream* s) {
   if (mf::fault_fires(mf::kFaultWaitTimeout)) *reinterpret_cast<volatile unsigned int*>(s->fault_host) = 1u;
-  if (__atomic_exchange_n(s->fault_host, 0u, __ATOMIC_ACQ_REL) == 0u) return MF_OK;
+  const unsigned int f = __atomic_exchange_n(s->fault_host, 0u, __ATOMIC_ACQ_REL);
+  if (f == 0u) return MF_OK;
+  if (f == mf::kFaultOutOfRange)
+    return fail(MF_ERR_CUDA, "checked build: an index outside its plane was caught (access skipped)");
   return fail(MF_ERR_TIMEOUT,
               "a bounded device wait of the tensor-core map kernel ran out: the frames concerned are "
               "marked MF_FRAME_TIMEOUT and bands of their maps hold NaN");

@@ -170,6 +170,35 @@ def test_windows_in_frame_accel(mf, window, smooth_len, kernel):
     assert info["n_valid"][-1] == window and M[-1].max() > 0.05
 
 
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+@pytest.mark.parametrize("window,normalize", [(24, "count"), (32, "count"), (20, "max")])
+def test_windows_above_16_with_16bit_storage(mf, storage, window, normalize):
+    """16-bit maps of 17..32-point windows (the 32-point map path), ACCEL points
+    in view, both normalisations; a width whose last strip leaves the frame."""
+    poses = _accelerating_walk(80)
+    rng = np.random.default_rng(2)
+    depth = rng.uniform(0.2, 5.0, (80, 240, 330)).astype(np.float32)
+    K = np.array([260.0, 260.0, 165.0, 120.0])
+    M, G, info, pts, ref = run_both(mf, poses, depth, K, 330, 240, window=window, smooth_len=15,
+                                    mode="accel", storage=storage, normalize=normalize)
+    if normalize == "count":
+        compare_all(M, G, info, pts, ref, K, storage=storage)
+    else:
+        intr = O.compensated_intrinsics(K, ref.p)
+        cst = O.OracleStream(O.Params(330, 240, window=window, smooth_len=15))
+        cst.push(poses, torch.from_numpy(depth).to(TDT[storage]).double().numpy(), K)
+        for n in range(ref.n_emitted):
+            rinfo, rp, Mr, Gr = ref.frame(n)
+            parity.check_frame(info[n], pts[n], rinfo, rp, intr, where=f"frame {n}", size=(330, 240))
+            mx = cst.frame(n)[2].max()
+            if rinfo["n_valid"] == 0 or abs(mx - O.NORM_FLOOR) <= 4 * parity.MAP_RTOL * O.NORM_FLOOR:
+                continue
+            div = mx if mx >= O.NORM_FLOOR else None
+            parity.check_map(M[n], Mr, storage, where=f"M frame {n}", divisor=div)
+            parity.check_map(G[n], Gr, storage, where=f"G frame {n}", divisor=div)
+    assert info["n_valid"][-1] == window and M[-1].max() > 0.05
+
+
 @pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("width,height", [(333, 197), (130, 70), (4, 3), (1, 1), (129, 65),
                                           (257, 129)])
