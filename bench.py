@@ -37,9 +37,10 @@ BYTES_PER_PX = 12  # depth read + focus map write + guided depth write (FP32)
 FRAME_BYTES = WIDTH * HEIGHT * BYTES_PER_PX
 # committed ncu summary and the sources it was taken from, per map kernel
 PROFILES = {
-    ("map_stream_kernel", "default"): ("map_kernel_1080p_f32.txt", ("mf_map_kernel.cu", "mf_map_unit.cuh")),
+    ("map_stream_kernel", "default"): ("map_kernel_1080p_f32.txt", ("mf_map_kernel.cuh", "mf_map_n16.cu",
+                                                                    "mf_map_unit.cuh")),
     ("map_stream_kernel", "heading"): ("map_kernel_1080p_f32_heading.txt",
-                                       ("mf_map_kernel.cu", "mf_map_unit.cuh")),
+                                       ("mf_map_kernel.cuh", "mf_map_n16.cu", "mf_map_unit.cuh")),
     ("map_tc_kernel", "default"): ("map_tc_kernel_1080p_f32.txt", ("mf_map_tc.cu", "mf_map_unit.cuh")),
 }
 # workloads of the 1080p line: the default (config 2: ACCEL, constant-speed

@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["mf_map_kernel.cu", "mf_map_tc.cu", "mf_pose_kernels.cu", "mf_stream.cpp", "mf_noalloc.cu",
+SOURCES = ["mf_map_kernel.cu", "mf_map_n8.cu", "mf_map_n16.cu", "mf_map_n32.cu", "mf_map_tc.cu", "mf_pose_kernels.cu", "mf_stream.cpp", "mf_noalloc.cu",
            "mf_engine.cpp", "mf_engine_kernels.cu", "mf_server.cpp", "mf_probe.cpp", "mf_fault.cpp", "mf_align.cu"]
 
 

@@ -39,8 +39,11 @@ constexpr float kCullBelow = 9.094947017729282e-13f;  // 2^-40
 
 // Resident CTAs per SM the persistent map kernels are compiled for: three
 // where 2 pixels per lane and at most 16 points keep the unit within 85
-// registers, else two (the 128-register unit).
-__host__ __device__ constexpr int unit_ctas_per_sm(int nmax, int cpt) { return cpt == 2 && nmax <= 16 ? 3 : 2; }
+// registers; one for 4 pixels per lane above 16 points (the column factors
+// alone take 128 registers); else two (the 128-register unit).
+__host__ __device__ constexpr int unit_ctas_per_sm(int nmax, int cpt) {
+  return cpt == 2 && nmax <= 16 ? 3 : (cpt == 4 && nmax > 16 ? 1 : 2);
+}
 
 // Depth rows in flight per warp; the ring packs a row at CPT x in_bytes
 // bytes per lane.  Rows of 16 bytes per lane: kStages.  Narrower rows: 2 KB
@@ -505,8 +508,8 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
   }
   if (strip_zero) dsrc = nullptr;
   // the first depth rows are in flight while the factors are computed
-#pragma unroll
   dq = reinterpret_cast<uintptr_t>(dsrc);  // after the strip test (dsrc may have been dropped)
+#pragma unroll
   for (int s = 0; s < S - 2; ++s) issue(false);
   const int nc = min(NMAX, (nk + 3) & ~3);
   for (int r = warp; r < rows; r += kMapThreads / 32)

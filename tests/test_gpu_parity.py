@@ -493,6 +493,35 @@ def test_translation_scale_invariance_bit_exact_on_gpu(mf):
         assert np.array_equal(x, y)
 
 
+def test_world_frame_change_and_mirror_symmetry_on_gpu(mf):
+    """Two symmetries of the method, checked on the CUDA path itself: a rigid
+    change of the world frame (T_t -> T_t G) leaves every output unchanged, and
+    mirroring the world about the camera's y-z plane (R -> S R S, t -> S t,
+    S = diag(-1, 1, 1)) mirrors the maps about the principal point's column
+    (cx = (W-1)/2), both within the map tolerance."""
+    poses = _accelerating_walk(60)
+    depth = np.ones((60, 64, 96), np.float32)
+    K = np.array([80.0, 80.0, 47.5, 31.5])
+    base = run_both(mf, poses, depth, K, 96, 64, window=8, smooth_len=9, mode="accel")
+    G = np.eye(4)
+    G[:3, :3] = rot_y(0.7) @ rot_x(-0.3)
+    G[:3, 3] = [12.0, -3.0, 40.0]
+    moved = np.stack([(O.to4x4(T) @ G)[:3] for T in poses])
+    Sm = np.diag([-1.0, 1.0, 1.0])
+    mirrored = poses.copy()
+    mirrored[:, :, :3] = Sm @ poses[:, :, :3] @ Sm
+    mirrored[:, :, 3] = poses[:, :, 3] @ Sm
+    a = run_both(mf, moved, depth, K, 96, 64, window=8, smooth_len=9, mode="accel")
+    m = run_both(mf, mirrored, depth, K, 96, 64, window=8, smooth_len=9, mode="accel")
+    assert base[2]["n_valid"].sum() > 100
+    for n in range(60):
+        parity.check_map(a[0][n], base[0][n].astype(np.float64), where=f"world frame M {n}")
+        parity.check_map(m[0][n][:, ::-1], base[0][n].astype(np.float64), where=f"mirror M {n}")
+        parity.check_map(m[1][n][:, ::-1], base[1][n].astype(np.float64), where=f"mirror G {n}")
+    for k in ("n_valid", "valid_mask", "status"):
+        assert np.array_equal(a[2][k], base[2][k]) and np.array_equal(m[2][k], base[2][k])
+
+
 def test_streams_alone_and_interleaved_identical(mf):
     dev = torch.device("cuda", 0)
     wa, wb = small_stream(seed=11, n_frames=30), small_stream(seed=12, n_frames=30)
