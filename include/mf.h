@@ -287,6 +287,29 @@ int mf_reset_stream(mf_stream* s);
  * the timed launches to finish). */
 int mf_stream_stats(mf_stream* s, mf_stats* out);
 
+/* Snapshot and restore of a stream's resident state, so that a live stream
+ * can move to another process, GPU or server.  The paper has no
+ * counterpart; the state is what the method carries between frames: the
+ * last window + smooth_len - 1 world poses (Eqs. 1-4 look that far back)
+ * with their bad-pose flags, the frame counters that place the next push's
+ * anchoring (Section 2.2), and, with MF_FLAG_DEPTH_ALIGN, the batch scale
+ * and the last `overlap` depth planes.
+ *   mf_stream_snapshot  writes the snapshot to host memory buf (cap bytes);
+ *                       buf = NULL only reports the size in *bytes.  Needs
+ *                       no pending frames (MF_ERR_NOT_READY otherwise: call
+ *                       mf_get_maps first); waits for the stream's work.
+ *   mf_stream_restore   loads a snapshot into a stream opened with the same
+ *                       descriptor fields (sizes, window, smooth_len, mode,
+ *                       pose frame, overlap, dtypes, normalisation, sigma /
+ *                       s / d0 parameters, depth alignment) that has taken no
+ *                       push yet or was reset (MF_ERR_NOT_READY otherwise);
+ *                       a different descriptor or a damaged snapshot gives
+ *                       MF_ERR_INVALID_ARG.  Synchronous.
+ * After a restore, the stream continues exactly as the snapshotted one
+ * would: the same later pushes give bit-identical maps and records. */
+int mf_stream_snapshot(mf_stream* s, void* buf, int64_t cap, int64_t* bytes);
+int mf_stream_restore(mf_stream* s, const void* buf, int64_t bytes);
+
 /* Wait for the stream's work, free everything the stream holds. */
 int mf_close_stream(mf_stream* s);
 

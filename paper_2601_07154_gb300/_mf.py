@@ -39,7 +39,7 @@ EXPORTED = ("mf_stream_desc_init", "mf_open_stream", "mf_push_frames", "mf_get_m
             "mf_server_latency", "mf_server_get_stats", "mf_server_close", "mf_clock_ns",
             "mf_engine_submit_batch", "mf_server_submit_batch", "mf_server_tune",
             "mf_probe_open", "mf_probe_stamp", "mf_probe_latency", "mf_probe_close",
-            "mf_set_fault")
+            "mf_set_fault", "mf_stream_snapshot", "mf_stream_restore")
 MF_ENGINE_NO_GRAPH = 2
 MF_ENGINE_NO_TUNE = 4
 MF_NOALLOC_MAX_FRAMES = 256
@@ -188,6 +188,8 @@ def _load():
     lib.mf_probe_latency.argtypes = [vp, ctypes.POINTER(MFLatencyStats), i32]
     lib.mf_probe_close.argtypes = [vp]
     lib.mf_set_fault.argtypes = [ctypes.c_char_p]
+    lib.mf_stream_snapshot.argtypes = [vp, vp, i64, ctypes.POINTER(i64)]
+    lib.mf_stream_restore.argtypes = [vp, vp, i64]
     for name in ("mf_open_stream", "mf_push_frames", "mf_get_maps", "mf_sync",
                  "mf_pending_frames", "mf_reset_stream", "mf_stream_stats", "mf_close_stream",
                  "mf_render_noalloc", "mf_engine_open", "mf_engine_add_stream",
@@ -198,7 +200,8 @@ def _load():
                  "mf_server_remove_stream", "mf_server_drain", "mf_server_latency",
                  "mf_server_get_stats", "mf_server_close", "mf_engine_submit_batch",
                  "mf_server_submit_batch", "mf_server_tune", "mf_probe_open", "mf_probe_stamp",
-                 "mf_probe_latency", "mf_probe_close", "mf_set_fault"):
+                 "mf_probe_latency", "mf_probe_close", "mf_set_fault", "mf_stream_snapshot",
+                 "mf_stream_restore"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -493,3 +496,18 @@ def mf_probe_close(p):
 def mf_set_fault(spec=None):
     """Host-side fault injection rules (see include/mf.h); None clears them."""
     _check(lib.mf_set_fault(spec.encode() if spec else None), "mf_set_fault")
+
+
+# ------------------------------------------------------- snapshot / restore --
+def mf_stream_snapshot(s):
+    """The stream's resident state as bytes (see include/mf.h)."""
+    n = ctypes.c_int64()
+    _check(lib.mf_stream_snapshot(s, None, 0, ctypes.byref(n)), "mf_stream_snapshot")
+    buf = ctypes.create_string_buffer(n.value)
+    _check(lib.mf_stream_snapshot(s, buf, n.value, ctypes.byref(n)), "mf_stream_snapshot")
+    return buf.raw[:n.value]
+
+
+def mf_stream_restore(s, blob):
+    blob = bytes(blob)
+    _check(lib.mf_stream_restore(s, blob, len(blob)), "mf_stream_restore")

@@ -8,6 +8,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstddef>
 #include <cstring>
 #include <deque>
 #include <new>
@@ -1076,6 +1077,154 @@ int mf_stream_stats(mf_stream* s, mf_stats* out) {
   out->device_bytes = s->device_bytes;
   out->last_map_kernel = s->last_map_kernel;
   out->reserved = 0;
+  return MF_OK;
+}
+
+namespace {
+
+// Layout of a stream snapshot: this header, then `hist` world poses (12
+// doubles each, oldest first), their bad flags (int32), then, with depth
+// alignment and a valid overlap, `overlap` depth planes.
+struct SnapHeader {
+  char magic[4];
+  int32_t version;
+  int64_t bytes;
+  // the descriptor fields the state depends on (must match on restore)
+  int32_t width, height, calib_width, calib_height, window, smooth_len, mode, pose_frame, overlap,
+      depth_dtype, map_dtype, normalize, align;
+  int32_t hist, ovl_valid, pad;
+  double sigma_rel, s_lo, s_hi, depth_ref_m;
+  int64_t emitted, pushes, pushed_frames;
+  double scale;
+};
+
+void snap_fill_desc(const mf_stream* s, SnapHeader* h) {
+  std::memset(h, 0, sizeof(*h));
+  std::memcpy(h->magic, "MFSN", 4);
+  h->version = 1;
+  h->width = s->d.width;
+  h->height = s->d.height;
+  h->calib_width = s->d.calib_width;
+  h->calib_height = s->d.calib_height;
+  h->window = s->d.window;
+  h->smooth_len = s->d.smooth_len;
+  h->mode = s->d.mode;
+  h->pose_frame = s->d.pose_frame;
+  h->overlap = s->d.overlap;
+  h->depth_dtype = s->d.depth_dtype;
+  h->map_dtype = s->d.map_dtype;
+  h->normalize = s->d.normalize;
+  h->align = s->align ? 1 : 0;
+  h->sigma_rel = s->d.sigma_rel;
+  h->s_lo = s->d.s_lo;
+  h->s_hi = s->d.s_hi;
+  h->depth_ref_m = s->d.depth_ref_m;
+}
+
+// Copies `count` ring entries starting at emitted-frame index `first`
+// between the device ring and host arrays (the ring wraps at its capacity).
+int ring_transfer(mf_stream* s, int64_t first, int64_t count, double* poses, int32_t* bad, bool to_host) {
+  int64_t done = 0;
+  while (done < count) {
+    const int64_t slot = (first + done) & (s->ring_cap - 1);
+    const int64_t run = std::min<int64_t>(count - done, s->ring_cap - slot);
+    double* dp = s->ring + slot * 12;
+    int32_t* db = s->ring_bad + slot;
+    if (to_host) {
+      MF_CUDA(cudaMemcpy(poses + done * 12, dp, (size_t)run * 12 * sizeof(double), cudaMemcpyDeviceToHost),
+              "snapshot copy");
+      MF_CUDA(cudaMemcpy(bad + done, db, (size_t)run * sizeof(int32_t), cudaMemcpyDeviceToHost), "snapshot copy");
+    } else {
+      MF_CUDA(cudaMemcpy(dp, poses + done * 12, (size_t)run * 12 * sizeof(double), cudaMemcpyHostToDevice),
+              "restore copy");
+      MF_CUDA(cudaMemcpy(db, bad + done, (size_t)run * sizeof(int32_t), cudaMemcpyHostToDevice), "restore copy");
+    }
+    done += run;
+  }
+  return MF_OK;
+}
+
+}  // namespace
+
+int mf_stream_snapshot(mf_stream* s, void* buf, int64_t cap, int64_t* bytes) {
+  if (!s || !bytes) return fail(MF_ERR_INVALID_ARG, "NULL stream or size");
+  if (s->emitted != s->rendered) return fail(MF_ERR_NOT_READY, "frames pending: call mf_get_maps first");
+  const int64_t hist = std::min<int64_t>(s->emitted, s->d.window + s->d.smooth_len - 1);
+  const bool ovl = s->align && s->ovl_valid;
+  const int64_t need = (int64_t)sizeof(SnapHeader) + hist * (12 * (int64_t)sizeof(double) + 4) +
+                       (ovl ? (int64_t)s->d.overlap * (int64_t)s->plane_in : 0);
+  *bytes = need;
+  if (!buf) return MF_OK;
+  if (cap < need) return fail(MF_ERR_INVALID_ARG, "snapshot buffer too small");
+  DeviceGuard guard(s->device);
+  MF_CUDA(cudaStreamSynchronize(s->st), "stream sync");
+  SnapHeader h;
+  snap_fill_desc(s, &h);
+  h.bytes = need;
+  h.hist = (int32_t)hist;
+  h.ovl_valid = ovl ? 1 : 0;
+  h.emitted = s->emitted;
+  h.pushes = s->pushes;
+  h.pushed_frames = s->pushed_frames;
+  h.scale = 1.0;
+  if (s->align) MF_CUDA(cudaMemcpy(&h.scale, s->scale_dev, sizeof(double), cudaMemcpyDeviceToHost), "snapshot copy");
+  char* p = static_cast<char*>(buf);
+  std::memcpy(p, &h, sizeof(h));
+  double* poses = reinterpret_cast<double*>(p + sizeof(h));
+  int32_t* bad = reinterpret_cast<int32_t*>(poses + hist * 12);
+  int rc = ring_transfer(s, s->emitted - hist, hist, poses, bad, true);
+  if (rc) return rc;
+  if (ovl)
+    MF_CUDA(cudaMemcpy(reinterpret_cast<char*>(bad + hist), s->ovl_prev, (size_t)s->d.overlap * s->plane_in,
+                       cudaMemcpyDeviceToHost),
+            "snapshot copy");
+  return MF_OK;
+}
+
+int mf_stream_restore(mf_stream* s, const void* buf, int64_t bytes) {
+  if (!s || !buf) return fail(MF_ERR_INVALID_ARG, "NULL stream or snapshot");
+  if (s->emitted != 0 || s->pushes != 0)
+    return fail(MF_ERR_NOT_READY, "restore into a stream that has taken no push (or was reset)");
+  if (bytes < (int64_t)sizeof(SnapHeader)) return fail(MF_ERR_INVALID_ARG, "not a stream snapshot");
+  SnapHeader h;
+  std::memcpy(&h, buf, sizeof(h));
+  SnapHeader mine;
+  snap_fill_desc(s, &mine);
+  if (std::memcmp(h.magic, "MFSN", 4) != 0 || h.version != 1 || h.bytes != bytes)
+    return fail(MF_ERR_INVALID_ARG, "not a stream snapshot of this version");
+  // every descriptor field the state depends on must match
+  const size_t fields = offsetof(SnapHeader, hist) - offsetof(SnapHeader, width);
+  if (std::memcmp(&h.width, &mine.width, fields) != 0 || h.sigma_rel != mine.sigma_rel ||
+      h.s_lo != mine.s_lo || h.s_hi != mine.s_hi || h.depth_ref_m != mine.depth_ref_m)
+    return fail(MF_ERR_INVALID_ARG, "the snapshot's stream descriptor differs from this stream's");
+  const int64_t max_hist = s->d.window + s->d.smooth_len - 1;
+  if (h.hist < 0 || h.hist > max_hist || h.hist > h.emitted || h.emitted < 0 ||
+      (h.ovl_valid && !s->align))
+    return fail(MF_ERR_INVALID_ARG, "inconsistent stream snapshot");
+  const int64_t need = (int64_t)sizeof(SnapHeader) + (int64_t)h.hist * (12 * (int64_t)sizeof(double) + 4) +
+                       (h.ovl_valid ? (int64_t)s->d.overlap * (int64_t)s->plane_in : 0);
+  if (need != bytes) return fail(MF_ERR_INVALID_ARG, "stream snapshot size mismatch");
+  DeviceGuard guard(s->device);
+  int rc = grow_ring(s, max_hist + 64);
+  if (rc) return rc;
+  MF_CUDA(cudaStreamSynchronize(s->st), "stream sync");
+  const char* p = static_cast<const char*>(buf);
+  const double* poses = reinterpret_cast<const double*>(p + sizeof(h));
+  const int32_t* bad = reinterpret_cast<const int32_t*>(poses + (int64_t)h.hist * 12);
+  rc = ring_transfer(s, h.emitted - h.hist, h.hist, const_cast<double*>(poses), const_cast<int32_t*>(bad),
+                     false);
+  if (rc) return rc;
+  if (s->align) {
+    MF_CUDA(cudaMemcpy(s->scale_dev, &h.scale, sizeof(double), cudaMemcpyHostToDevice), "restore copy");
+    s->ovl_valid = h.ovl_valid != 0;
+    if (s->ovl_valid)
+      MF_CUDA(cudaMemcpy(s->ovl_prev, reinterpret_cast<const char*>(bad + h.hist),
+                         (size_t)s->d.overlap * s->plane_in, cudaMemcpyHostToDevice),
+              "restore copy");
+  }
+  s->emitted = s->rendered = h.emitted;
+  s->pushes = h.pushes;
+  s->pushed_frames = h.pushed_frames;
   return MF_OK;
 }
 

@@ -124,6 +124,18 @@ class MotionFocusStream:
                   if pts is not None else None)
         return M, G, info_np, pts_np
 
+    def snapshot(self):
+        """Resident state as bytes (no pending frames): window history, frame
+        counters, depth alignment state."""
+        with torch.cuda.device(self.device):
+            return _mf.mf_stream_snapshot(self.handle)
+
+    def restore(self, blob):
+        """Load a snapshot taken from a stream with the same options (this
+        stream must not have taken a push yet, or must be reset)."""
+        with torch.cuda.device(self.device):
+            _mf.mf_stream_restore(self.handle, blob)
+
     def sync(self, timeout_ns=-1):
         _mf.mf_sync(self.handle, timeout_ns)
 
