@@ -57,8 +57,7 @@ __global__ void __launch_bounds__(kEngPtsWarps * 32) engine_points_kernel(Engine
 template <typename TIn, typename TOut, int NMAX, int CPT, int PATH>
 __global__ void __launch_bounds__(kMapThreads, unit_ctas_per_sm(NMAX, CPT)) engine_map_kernel(EngineKernelArgs a) {
   extern __shared__ float4 smem4[];
-  __shared__ PointsSmem<kMaxPts> P;
-  __shared__ int s_kept;
+  __shared__ PointsSmem<kMaxPts> P[kMapThreads / 32];
   __shared__ uint4 zeros[kZeroBytes / 16];
   init_zero_source(zeros);
   constexpr int kGroupW = 8 * 32 * CPT;
@@ -103,7 +102,7 @@ __global__ void __launch_bounds__(kMapThreads, unit_ctas_per_sm(NMAX, CPT)) engi
     ug.rows = min(fr.band_h, ug.height - ug.y0);
     ug.d0 = sp.d0;
     ug.gx0 = g * kGroupW;
-    map_unit<NMAX, CPT, TIn, TOut>(ug, Ey, my_ring, P, s_kept, zeros);
+    map_unit<NMAX, CPT, TIn, TOut>(ug, Ey, my_ring, P, zeros);
     u = next_unit(a.sched + PATH, claim, units, s_next, k);
   }
   bulk_wait_all();

@@ -264,8 +264,7 @@ __global__ void __launch_bounds__(kMapThreads, unit_ctas_per_sm(NMAX, CPT))
   extern __shared__ float4 smem4[];
   float* Ey = reinterpret_cast<float*>(smem4);                          // [band_h][NMAX]
   uint4* ring = reinterpret_cast<uint4*>(Ey + (size_t)band_h * NMAX);   // [8][stages][32]
-  __shared__ PointsSmem<kMaxPts> P;
-  __shared__ int s_kept;
+  __shared__ PointsSmem<kMaxPts> P[kMapThreads / 32];
   __shared__ uint4 zeros[kZeroBytes / 16];
   init_zero_source(zeros);
   constexpr int kGroupW = kGroupStrips * 32 * CPT;
@@ -295,7 +294,7 @@ __global__ void __launch_bounds__(kMapThreads, unit_ctas_per_sm(NMAX, CPT))
     ug.rows = min(band_h, p.height - ug.y0);
     ug.gx0 = g * kGroupW;
     ug.d0 = ug.rec->d0;
-    map_unit<NMAX, CPT, TIn, TOut, MODE>(ug, Ey, my_ring, P, s_kept, zeros);
+    map_unit<NMAX, CPT, TIn, TOut, MODE>(ug, Ey, my_ring, P, zeros);
     u = next_unit(p.sched, claim, units, s_next, k);
   }
   bulk_wait_all();

@@ -75,6 +75,7 @@ __device__ __forceinline__ uint4 ring_row(const uint4* ring, int slot) {
 template <int NMAX>
 struct PointsSmem {
   float uhi[NMAX], ulo[NMAX], vhi[NMAX], vlo[NMAX], chi[NMAX], clo[NMAX];
+  int kept;  // entries in use (the map unit's lists)
 };
 
 // exp(-(q - hi - lo)^2 * (chi + clo)) for an integer-valued q.  hi lies on a
@@ -202,6 +203,7 @@ __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wa
 __device__ __forceinline__ void init_zero_source(uint4* zeros) {
   for (int i = threadIdx.x; i < kZeroBytes / 16; i += blockDim.x) zeros[i] = make_uint4(0u, 0u, 0u, 0u);
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncthreads();
 }
 
 template <int N>
@@ -364,7 +366,7 @@ constexpr int kUnitScaled = 2;
 
 template <int NMAX, int CPT, typename TIn, typename TOut, int MODE = kUnitFull>
 __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* my_ring,
-                                         PointsSmem<kMaxPts>& P, int& s_kept, const uint4* zeros) {
+                                         PointsSmem<kMaxPts>* Pw, const uint4* zeros) {
   constexpr int kInBytes = CPT * (int)sizeof(TIn);
   constexpr int kStrip = 32 * CPT;
   constexpr int S = ring_stages(CPT, (int)sizeof(TIn), NMAX);
@@ -392,8 +394,17 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
     ++rq;
     dq += dstride;
   };
-  // The ring is this warp's own and the previous unit drained it.
-  __syncthreads();  // the previous unit is done with P and Ey
+  // The ring is this warp's own and the previous unit drained it.  Every
+  // warp culls the points itself into its own copy of the kept list (the
+  // same list in every warp), so no warp waits for another before the row
+  // factors; the caller's barrier between units (next_unit) ordered every
+  // warp's last use of the previous unit's tables before the writes below.
+  // The one-CTA-per-SM unit (4 columns per lane above 16 points) keeps one
+  // list, culled by warp 0 between two barriers: its register-bound code
+  // measured 5 % slower with per-warp lists (HEADING BF16, window 32),
+  // where the others gained up to 2 %.
+  constexpr bool kOwnList = !(CPT == 4 && NMAX > 16);
+  if (!kOwnList) __syncthreads();  // the previous unit is done with P and Ey
 
   FrameRec* rec = ug.rec;
   const int n = rec->n_valid;
@@ -429,7 +440,9 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
     if (MODE != kUnitScaled)
       publish_key(rec, col_ok ? (unsigned long long)(0xffffffffu - (unsigned)(y0 * ug.width + xc)) : 0ull, n > 0);
   };
-  if (warp == 0) {
+  PointsSmem<kMaxPts>& P = Pw[kOwnList ? warp : 0];
+  int nk;  // <= NMAX: n never exceeds the window's bucket
+  if (kOwnList || warp == 0) {
     bool keep = false;
     float uh = 0.f, ul = 0.f, vh = 0.f, vl = 0.f, ch = 0.f, cl = 0.f;
     if (lane < n) {
@@ -455,10 +468,14 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
       P.chi[pos] = ch;
       P.clo[pos] = cl;
     }
-    if (lane == 0) s_kept = __popc(mask);
+    nk = __popc(mask);
+    if (!kOwnList && lane == 0) P.kept = nk;
+    __syncwarp();
   }
-  __syncthreads();
-  const int nk = s_kept;  // <= NMAX: n never exceeds the window's bucket
+  if (!kOwnList) {
+    __syncthreads();  // warp 0's list is complete
+    nk = P.kept;
+  }
   // Zero rows by bulk copy need 16-byte aligned rows in both map planes.
   const bool bulk = zeros != nullptr && ((size_t)ug.width * sizeof(TOut)) % 16 == 0 &&
                     ((uintptr_t)ug.M % 16) == 0 && ((uintptr_t)ug.G % 16) == 0;
