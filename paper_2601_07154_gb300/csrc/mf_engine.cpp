@@ -436,7 +436,7 @@ int tune_class(mf_engine* e, int width, int height, int window, int* band_out) {
       const double sig = 0.1 * fx * (0.5 + fu);
       r.ux_hi[i] = (float)(width * (0.1 + 0.8 * fu));
       r.vy_hi[i] = (float)(height * (0.1 + 0.8 * fv));
-      const double c = 1.0 / (2.0 * sig * sig);
+      const double c = 1.4426950408889634 / (2.0 * sig * sig);  // log2(e) / (2 sigma^2)
       r.c_hi[i] = (float)c;
       r.c_lo[i] = (float)(c - (double)(float)c);
     }

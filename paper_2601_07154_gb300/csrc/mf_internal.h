@@ -32,7 +32,8 @@ constexpr double kValidRelZ = 1e-3;
 // block holds the map kernel's operands for the valid points, compacted in
 // slot order: u = ux_hi + ux_lo and v = vy_hi + vy_lo split so that the
 // integer pixel coordinate minus the high part is exact in FP32, and the
-// Gaussian's 1 / (2 sigma^2) as a float pair c_hi + c_lo.
+// Gaussian's log2(e) / (2 sigma^2) as a float pair c_hi + c_lo (the map
+// kernels take exp(-d^2 / (2 sigma^2)) as 2^-(d^2 c)).
 struct alignas(16) FrameRec {
   float ux_hi[kMaxPts], ux_lo[kMaxPts];
   float vy_hi[kMaxPts], vy_lo[kMaxPts];

@@ -78,10 +78,19 @@ struct PointsSmem {
   int kept;  // entries in use (the map unit's lists)
 };
 
-// exp(-(q - hi - lo)^2 * (chi + clo)) for an integer-valued q.  hi lies on a
-// 2^-8 grid with |hi| < 2^15, so q - hi is exact; the square is carried as a
-// compensated pair and 1/(2 sigma^2) as a float pair, which keeps the
-// exponent's relative error near one FP32 rounding before expf (<= 2 ulp).
+// 2^x by the hardware base-2 exponential (PTX ex2.approx.ftz: relative
+// error about 2^-22; results below 2^-126 flush to 0).
+__device__ __forceinline__ float exp2_hw(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// exp(-(q - hi - lo)^2 / (2 sigma^2)) = 2^-((q - hi - lo)^2 (chi + clo)) for an
+// integer-valued q, with chi + clo = log2(e) / (2 sigma^2) as a float pair.
+// hi lies on a 2^-8 grid with |hi| < 2^15, so q - hi is exact; the square is
+// carried as a compensated pair, which keeps the exponent's relative error
+// near one FP32 rounding before the base-2 exponential.
 __device__ __forceinline__ float gauss_factor(float q, float hi, float lo, float chi, float clo) {
   const float dh = q - hi;
   const float p2 = dh * dh;
@@ -90,7 +99,7 @@ __device__ __forceinline__ float gauss_factor(float q, float hi, float lo, float
   qq = fmaf(lo, lo, qq);
   const float t1 = fmaf(clo, p2, chi * qq);
   const float a = fmaf(chi, p2, t1);
-  return expf(-a);
+  return exp2_hw(-a);
 }
 
 __device__ __forceinline__ float2 ffma2(float2 a, float b, float2 c) {

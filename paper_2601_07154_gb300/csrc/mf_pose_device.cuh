@@ -245,7 +245,9 @@ __device__ __forceinline__ void frame_points(const double* ring, const int32_t* 
     split_coord(v, hi, lo);
     rec->vy_hi[pos] = hi;
     rec->vy_lo[pos] = lo;
-    double c = 1.0 / (2.0 * sig * sig);
+    // log2(e) / (2 sigma^2): the map kernels evaluate the Gaussian as a
+    // power of 2
+    double c = 1.4426950408889634 / (2.0 * sig * sig);
     c = fmin(c, 1e30);
     const float chi = (float)c;
     rec->c_hi[pos] = chi;
