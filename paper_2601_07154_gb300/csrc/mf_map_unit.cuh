@@ -79,7 +79,7 @@ struct PointsSmem {
 };
 
 // 2^x by the hardware base-2 exponential (PTX ex2.approx.ftz: relative
-// error about 2^-22; results below 2^-126 flush to 0).
+// error of a few ulp; results below 2^-126 flush to 0).
 __device__ __forceinline__ float exp2_hw(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
