@@ -12,7 +12,7 @@ def pytest_configure(config):
 
 
 def pytest_terminal_summary(terminalreporter, exitstatus, config):
-    """The largest GPU-vs-oracle coordinate errors of the session (pixels)."""
+    """The largest GPU-vs-oracle coordinate (pixels) and map errors of the session."""
     parity = sys.modules.get("tests.parity")
     if parity is None:
         return
@@ -20,3 +20,6 @@ def pytest_terminal_summary(terminalreporter, exitstatus, config):
            for k, v in parity.COORD_ERR.items() if v[2]}
     if rec:
         terminalreporter.write_line("COORD_ERROR " + json.dumps(rec))
+    maps = {k: {"max_rel": v[0], "max_abs": v[1], "pixels": v[2]} for k, v in parity.MAP_ERR.items() if v[2]}
+    if maps:
+        terminalreporter.write_line("MAP_ERROR " + json.dumps(maps))

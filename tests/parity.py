@@ -11,8 +11,10 @@ and no FP64 pipeline holds a flat 1e-3 px at a thousand focal lengths.
 relative, plus fp16's subnormal step.
 
 Every coordinate comparison is recorded in ``COORD_ERR`` (largest |du|,
-|dv| inside and outside the image, and how many points); the test session
-prints the record at its end.
+|dv| inside and outside the image, and how many points), every map
+comparison in ``MAP_ERR`` (largest relative error where the reference
+exceeds 1e-6, largest absolute error, pixels compared, per storage); the
+test session prints both records at its end.
 """
 import numpy as np
 
@@ -27,6 +29,8 @@ INT_FIELDS = ("frame_index", "status", "n_valid", "valid_mask", "focus_valid",
 
 # largest coordinate errors seen by this process: {"in_image"|"off_image": [du, dv, count]}
 COORD_ERR = {"in_image": [0.0, 0.0, 0], "off_image": [0.0, 0.0, 0]}
+# largest map errors seen by this process: {storage[+"/max"]: [rel, abs, pixels]}
+MAP_ERR = {}
 
 
 def in_image(u, v, size):
@@ -116,7 +120,14 @@ def check_argmax(info, M_ref, n_valid, storage="f32", where=""):
 
 def check_map(got, ref, storage="f32", where="", divisor=None):
     got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
     err = np.abs(got - ref)
+    big = ref > 1e-6
+    rec = MAP_ERR.setdefault(storage + ("/max" if divisor is not None else ""), [0.0, 0.0, 0])
+    if err.size:
+        rec[0] = max(rec[0], float((err[big] / ref[big]).max(initial=0.0)))
+        rec[1] = max(rec[1], float(err.max()))
+        rec[2] += int(err.size)
     tol = map_tol(ref, storage, divisor)
     bad = err > tol
     if bad.any():
