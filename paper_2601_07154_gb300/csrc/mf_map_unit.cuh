@@ -102,6 +102,7 @@ __device__ __forceinline__ float gauss_factor(float q, float hi, float lo, float
   return exp2_hw(-a);
 }
 
+
 __device__ __forceinline__ float2 ffma2(float2 a, float b, float2 c) {
   float2 d;
   asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
@@ -127,6 +128,44 @@ __device__ __forceinline__ float2 fmul2(float2 a, float b) {
       : "=f"(d.x), "=f"(d.y)
       : "f"(a.x), "f"(a.y), "f"(b));
   return d;
+}
+
+// Lane-wise a + b, a * b and fma(a, b, c) on f32x2 pairs (IEEE round to
+// nearest on each lane: the values of the scalar operations).
+__device__ __forceinline__ float2 fadd2v(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 fmul2v(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 ffma2v(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "mov.b64 rc, {%6, %7};\n\tfma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+
+// gauss_factor at columns q0 and q0 + 1 (q0 integer-valued), the exponent's
+// steps on f32x2 pairs: the same operations in the same order on each lane,
+// with the signs carried through exact negations, so the same values.
+__device__ __forceinline__ float2 gauss_pair(float q0, float hi, float lo, float chi, float clo) {
+  const float2 dh = fadd2v(make_float2(q0, q0 + 1.0f), make_float2(-hi, -hi));  // exact
+  const float2 p2 = fmul2v(dh, dh);
+  const float2 e2 = ffma2v(dh, dh, fmul2v(p2, make_float2(-1.0f, -1.0f)));        // dh^2 - p2
+  float2 qq = ffma2v(fmul2v(dh, make_float2(-2.0f, -2.0f)), make_float2(lo, lo), e2);
+  qq = ffma2v(make_float2(lo, lo), make_float2(lo, lo), qq);
+  const float2 nt1 = ffma2v(make_float2(-clo, -clo), p2, fmul2v(make_float2(-chi, -chi), qq));
+  const float2 na = ffma2v(make_float2(-chi, -chi), p2, nt1);                      // -a
+  return make_float2(exp2_hw(na.x), exp2_hw(na.y));
 }
 
 // max(a, b, c) in one instruction (three-input max.f32 of sm_100 and later).
@@ -549,12 +588,9 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
     if (i < nc) {
 #pragma unroll
       for (int c = 0; c < CPT / 2; ++c) {
-        float e0 = 0.f, e1 = 0.f;
-        if (i < nk && col_ok && !strip_zero) {
-          e0 = gauss_factor((float)(xc + 2 * c), P.uhi[i], P.ulo[i], P.chi[i], P.clo[i]);
-          e1 = gauss_factor((float)(xc + 2 * c + 1), P.uhi[i], P.ulo[i], P.chi[i], P.clo[i]);
-        }
-        ex[i][c] = make_float2(e0, e1);
+        ex[i][c] = i < nk && col_ok && !strip_zero
+                       ? gauss_pair((float)(xc + 2 * c), P.uhi[i], P.ulo[i], P.chi[i], P.clo[i])
+                       : make_float2(0.f, 0.f);
       }
     }
   }
