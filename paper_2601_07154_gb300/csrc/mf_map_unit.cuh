@@ -577,11 +577,21 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
 #pragma unroll
   for (int s = 0; s < S - 2; ++s) issue(false);
   const int nc = min(NMAX, (nk + 3) & ~3);
-  for (int r = warp; r < rows; r += kMapThreads / 32)
-    for (int i = lane; i < nc; i += 32)
-      Ey[r * NMAX + i] =
-          i < nk ? gauss_factor((float)(y0 + r), P.vhi[i], P.vlo[i], P.chi[i], P.clo[i]) * inv_n
-                 : 0.0f;
+  // Row factors times 1/Z, two rows per entry and NMAX entries per row
+  // pair, so that every lane has work also below 32 points: entry k is point
+  // k % NMAX of rows 2 (k / NMAX) and 2 (k / NMAX) + 1.
+  for (int k = tid; k < ((rows + 1) >> 1) * NMAX; k += kMapThreads) {
+    const int i = k & (NMAX - 1), r = 2 * (k / NMAX);
+    if (i >= nc) continue;
+    float2 g = make_float2(0.0f, 0.0f);
+    if (i < nk) {
+      g = gauss_pair((float)(y0 + r), P.vhi[i], P.vlo[i], P.chi[i], P.clo[i]);
+      g.x *= inv_n;
+      g.y *= inv_n;
+    }
+    Ey[r * NMAX + i] = g.x;
+    if (r + 1 < rows) Ey[(r + 1) * NMAX + i] = g.y;
+  }
   float2 ex[NMAX][CPT / 2];
 #pragma unroll
   for (int i = 0; i < NMAX; ++i) {
