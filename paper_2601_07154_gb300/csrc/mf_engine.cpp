@@ -127,7 +127,7 @@ struct Slot {
 int path_cpt(int path, int map_dtype) {
   return path ? mf::engine_wide_cpt((int)dtype_bytes(map_dtype)) : mf::kEngineCPT;
 }
-int path_group_w(int path, int map_dtype) { return 8 * 32 * path_cpt(path, map_dtype); }
+int path_group_w(int path, int map_dtype) { return mf::kGroupStrips * 32 * path_cpt(path, map_dtype); }
 
 // The 16-point path serves windows up to 16 points on widths divisible by
 // its columns per lane; every other stream takes the 32-point path.

@@ -15,7 +15,6 @@ namespace mf {
 // per lane, fewer instructions per pixel; FP32 maps: 2, whose smaller unit
 // fits three CTAs per SM).
 constexpr int kEngineCPT = 2;                           // columns per lane, 32-point path
-constexpr int kEngineGroupW = 8 * 32 * kEngineCPT;      // columns per map unit
 constexpr int kEngineWideNMAX = 16;
 __host__ __device__ constexpr int engine_wide_cpt(int map_bytes) { return map_bytes == 4 ? 2 : 4; }
 constexpr int kEnginePaths = 2;                         // 0: 32-point, 1: 16-point

@@ -55,12 +55,12 @@ __global__ void __launch_bounds__(kEngPtsWarps * 32) engine_points_kernel(Engine
 // frames.  Each path is its own kernel: one kernel holding both the 16- and
 // the 32-point unit would not fit the register budget.
 template <typename TIn, typename TOut, int NMAX, int CPT, int PATH>
-__global__ void __launch_bounds__(kMapThreads, unit_ctas_per_sm(NMAX, CPT)) engine_map_kernel(EngineKernelArgs a) {
+__global__ void __launch_bounds__(kUnitThreads, unit_ctas_per_sm(NMAX, CPT)) engine_map_kernel(EngineKernelArgs a) {
   extern __shared__ float4 smem4[];
-  __shared__ PointsSmem<kMaxPts> P[kMapThreads / 32];
+  __shared__ PointsSmem<kMaxPts> P[kGroupStrips];
   __shared__ uint4 zeros[kZeroBytes / 16];
   init_zero_source(zeros);
-  constexpr int kGroupW = 8 * 32 * CPT;
+  constexpr int kGroupW = kGroupStrips * 32 * CPT;
   const TickHeader* tab = a.table;
   const int nf = tab->n_frames_path[PATH];
   const long long units = tab->n_units_path[PATH];
@@ -127,12 +127,12 @@ struct MapKernel {
   // resident CTAs on the current device (shared memory limit raised there)
   static int grid() {
     const KernelFit f = host_kernel_fit(
-        reinterpret_cast<const void*>(engine_map_kernel<TIn, TOut, kN, kC, PATH>), kMapThreads, smem(),
+        reinterpret_cast<const void*>(engine_map_kernel<TIn, TOut, kN, kC, PATH>), kUnitThreads, smem(),
         smem());
     return f.sms * f.per_sm;
   }
   static void launch(const EngineKernelArgs& a, int grid, cudaStream_t st) {
-    engine_map_kernel<TIn, TOut, kN, kC, PATH><<<grid, kMapThreads, smem(), st>>>(a);
+    engine_map_kernel<TIn, TOut, kN, kC, PATH><<<grid, kUnitThreads, smem(), st>>>(a);
   }
 };
 

@@ -16,10 +16,11 @@ namespace mf {
 constexpr int kMaxPts = MF_MAX_WINDOW;   // N motion points per frame
 constexpr int kMaxHist = MF_MAX_HISTORY; // W + K - 1 poses per frame
 constexpr int kTileW = 128;              // map-kernel tile width (32 lanes x 4 px)
-constexpr int kMapThreads = 256;         // 8 warps per map CTA
+constexpr int kMapThreads = 256;         // 8 warps per CTA of the tiled map kernel
 constexpr int kStages = 4;               // depth ring rows per map warp at 16 B per lane (power of 2)
 constexpr int kBandMax = 256;            // largest rows per map unit
 constexpr int kGroupStrips = 8;          // strips (one per warp) per map unit
+constexpr int kUnitThreads = 32 * kGroupStrips;  // threads per CTA of the unit map kernels
 
 // Thresholds of the motion-point validity test (Section 2.3, Eq. 6 readings).
 constexpr double kRigidTol = 1e-6;

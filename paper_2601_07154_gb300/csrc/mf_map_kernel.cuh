@@ -259,12 +259,12 @@ __global__ void __launch_bounds__(kMapThreads) map_kernel(MapParams p) {
 // up to 256 rows x group of 8 strips) in frame order from the dynamic
 // schedule; map_unit does the work.
 template <int NMAX, int CPT, typename TIn, typename TOut, int MODE>
-__global__ void __launch_bounds__(kMapThreads, unit_ctas_per_sm(NMAX, CPT))
+__global__ void __launch_bounds__(kUnitThreads, unit_ctas_per_sm(NMAX, CPT))
     map_stream_kernel(MapParams p, int band_h) {
   extern __shared__ float4 smem4[];
   float* Ey = reinterpret_cast<float*>(smem4);                          // [band_h][NMAX]
   uint4* ring = reinterpret_cast<uint4*>(Ey + (size_t)band_h * NMAX);   // [8][stages][32]
-  __shared__ PointsSmem<kMaxPts> P[kMapThreads / 32];
+  __shared__ PointsSmem<kMaxPts> P[kGroupStrips];
   __shared__ uint4 zeros[kZeroBytes / 16];
   init_zero_source(zeros);
   constexpr int kGroupW = kGroupStrips * 32 * CPT;
@@ -320,9 +320,9 @@ NormalizeParams normalize_params(const MapParams& p);
 template <typename K>
 void launch_persistent(K k, size_t smem_max, long long units, size_t smem, const MapParams& p,
                        int band_h, cudaStream_t st) {
-  const KernelFit f = host_kernel_fit(reinterpret_cast<const void*>(k), kMapThreads, smem_max, smem_max);
+  const KernelFit f = host_kernel_fit(reinterpret_cast<const void*>(k), kUnitThreads, smem_max, smem_max);
   const long long grid = std::min<long long>(units, (long long)f.sms * f.per_sm);
-  k<<<(unsigned)grid, kMapThreads, smem, st>>>(p, band_h);
+  k<<<(unsigned)grid, kUnitThreads, smem, st>>>(p, band_h);
 }
 
 // One launch (or, for MF_NORM_MAX, a max-only pass then a scaled pass) of

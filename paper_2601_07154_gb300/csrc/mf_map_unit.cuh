@@ -37,22 +37,26 @@ namespace mf {
 
 constexpr float kCullBelow = 9.094947017729282e-13f;  // 2^-40
 
-// Resident CTAs per SM the persistent map kernels are compiled for: three
+// Resident warps per SM the persistent map kernels are compiled for: 24
 // where 2 pixels per lane and at most 16 points keep the unit within 85
-// registers; one for 4 pixels per lane above 16 points (the column factors
-// alone take 128 registers); else two (the 128-register unit).
+// registers; 8 for 4 pixels per lane above 16 points (the column factors
+// alone take 128 registers); else 16 (the 128-register unit).  CTAs per SM:
+// that over the warps of a CTA.
+__host__ __device__ constexpr int unit_warps_per_sm(int nmax, int cpt) {
+  return cpt == 2 && nmax <= 16 ? 24 : (cpt == 4 && nmax > 16 ? 8 : 16);
+}
 __host__ __device__ constexpr int unit_ctas_per_sm(int nmax, int cpt) {
-  return cpt == 2 && nmax <= 16 ? 3 : (cpt == 4 && nmax > 16 ? 1 : 2);
+  return unit_warps_per_sm(nmax, cpt) / kGroupStrips;
 }
 
 // Depth rows in flight per warp; the ring packs a row at CPT x in_bytes
 // bytes per lane.  Rows of 16 bytes per lane: kStages.  Narrower rows: 2 KB
-// per warp where three CTAs share an SM, 4 KB where two do (1080p frames:
-// the 4 KB ring gains 2-6 % with two CTAs per SM and loses about 1 % with
-// three).
+// per warp where 24 warps share an SM, 4 KB where 16 or 8 do (1080p frames:
+// the 4 KB ring gains 2-6 % at 16 warps per SM and loses about 1 % at
+// 24).
 __host__ __device__ constexpr int ring_stages(int cpt, int in_bytes, int nmax) {
   return cpt * in_bytes >= 16 ? kStages
-                              : (unit_ctas_per_sm(nmax, cpt) == 3 ? 2048 : 4096) / (32 * cpt * in_bytes);
+                              : (unit_warps_per_sm(nmax, cpt) == 24 ? 2048 : 4096) / (32 * cpt * in_bytes);
 }
 
 // A lane's depth bytes of ring row slot `slot` (rows packed at BYTES per lane).
@@ -235,8 +239,9 @@ __device__ __forceinline__ void cp_async(void* dst, const void* src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 
 // Zero rows through the bulk-copy engine: a shared-memory source of zeros,
-// at least one unit row wide (8 strips x 32 lanes x 4 columns x 4 bytes).
-constexpr int kZeroBytes = 8 * 32 * 4 * 4;
+// at least one unit row wide (kGroupStrips strips x 32 lanes x 4 columns x
+// 4 bytes).
+constexpr int kZeroBytes = kGroupStrips * 32 * 4 * 4;
 __device__ __forceinline__ void bulk_copy_s2g(void* dst, const void* src_smem, uint32_t bytes) {
   asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
                "r"((uint32_t)__cvta_generic_to_shared(src_smem)), "r"(bytes)
@@ -540,7 +545,7 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
       const int cols = min(kGroupStrips * kStrip, ug.width - ug.gx0);
       const uint32_t bytes = (uint32_t)(cols * (int)sizeof(TOut));
       const size_t first = (size_t)y0 * ug.width + ug.gx0;
-      for (int r = tid; r < rows; r += kMapThreads) {
+      for (int r = tid; r < rows; r += kUnitThreads) {
         const size_t at = (first + (size_t)r * ug.width) * sizeof(TOut);
         if (!in_plane(ug, y0 + r, ug.gx0, cols)) continue;
         if (ug.M) bulk_copy_s2g(ug.M + at, zeros, bytes);
@@ -580,7 +585,7 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
   // Row factors times 1/Z, two rows per entry and NMAX entries per row
   // pair, so that every lane has work also below 32 points: entry k is point
   // k % NMAX of rows 2 (k / NMAX) and 2 (k / NMAX) + 1.
-  for (int k = tid; k < ((rows + 1) >> 1) * NMAX; k += kMapThreads) {
+  for (int k = tid; k < ((rows + 1) >> 1) * NMAX; k += kUnitThreads) {
     const int i = k & (NMAX - 1), r = 2 * (k / NMAX);
     if (i >= nc) continue;
     float2 g = make_float2(0.0f, 0.0f);
@@ -738,7 +743,7 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
 // every warp's depth ring.
 __host__ __device__ constexpr size_t unit_smem_bytes(int nmax, int band_h, int cpt, int in_bytes) {
   return (size_t)band_h * nmax * 4 +
-         (size_t)(kMapThreads / 32) * ring_stages(cpt, in_bytes, nmax) * 32 * cpt * in_bytes;
+         (size_t)kGroupStrips * ring_stages(cpt, in_bytes, nmax) * 32 * cpt * in_bytes;
 }
 
 // Dynamic unit schedule of the persistent map kernels.  CTA c starts on
