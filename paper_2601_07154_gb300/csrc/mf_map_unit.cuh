@@ -351,7 +351,7 @@ __device__ __forceinline__ void accum_two_rows(const float2 (&ex)[NMAX][CPT / 2]
   const float4* e0p = reinterpret_cast<const float4*>(ey0);
   const float4* e1p = reinterpret_cast<const float4*>(ey1);
 #pragma unroll
-  for (int i = 0; i < NMAX; i += 4) {
+  for (int i = 0; i < (NC ? NC : NMAX); i += 4) {
     if (NC == 0 && i >= nc) break;
     const float4 e = e0p[i >> 2];
     const float4 f = e1p[i >> 2];
@@ -587,8 +587,7 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
   // k % NMAX of rows 2 (k / NMAX) and 2 (k / NMAX) + 1.
   for (int k = tid; k < ((rows + 1) >> 1) * NMAX; k += kUnitThreads) {
     const int i = k & (NMAX - 1), r = 2 * (k / NMAX);
-    if (i >= nc) continue;
-    float2 g = make_float2(0.0f, 0.0f);
+    float2 g = make_float2(0.0f, 0.0f);  // zeros past the kept points (padded trip counts)
     if (i < nk) {
       g = gauss_pair((float)(y0 + r), P.vhi[i], P.vlo[i], P.chi[i], P.clo[i]);
       g.x *= inv_n;
@@ -600,13 +599,11 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
   float2 ex[NMAX][CPT / 2];
 #pragma unroll
   for (int i = 0; i < NMAX; ++i) {
-    if (i < nc) {
 #pragma unroll
-      for (int c = 0; c < CPT / 2; ++c) {
-        ex[i][c] = i < nk && col_ok && !strip_zero
-                       ? gauss_pair((float)(xc + 2 * c), P.uhi[i], P.ulo[i], P.chi[i], P.clo[i])
-                       : make_float2(0.f, 0.f);
-      }
+    for (int c = 0; c < CPT / 2; ++c) {
+      ex[i][c] = i < nk && col_ok && !strip_zero
+                     ? gauss_pair((float)(xc + 2 * c), P.uhi[i], P.ulo[i], P.chi[i], P.clo[i])
+                     : make_float2(0.f, 0.f);
     }
   }
   __syncthreads();  // Ey complete
@@ -653,8 +650,9 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
   // before rows r, r+1 are read.  FAST: depth, M and G all present, every
   // lane's columns inside the frame and an even number of rows (the common
   // case), so a step carries no null, column or last-row checks.
-  auto rows_loop = [&](auto fast_tag) {
+  auto rows_loop = [&](auto fast_tag, auto nc_tag) {
     constexpr bool FAST = decltype(fast_tag)::value;
+    constexpr int NCF = decltype(nc_tag)::value;  // > 0: the sums' trip count (padded)
     size_t off = 0;  // output rows advance by a stride: no per-row 64-bit multiply
     for (int r = 0; r < rows; r += 2, off += 2 * ostride) {
       const bool TWO = FAST || r + 1 < rows;
@@ -669,7 +667,10 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
         if (TWO) Vec<TIn, CPT>::unpack(ring_row<kInBytes>(my_ring, ((r + 1) & (S - 1)) * 32 + lane), d1v);
       }
       float2 a[CPT / 2], b[CPT / 2];
-      sums(r, TWO, a, b);
+      if constexpr (NCF > 0)
+        accum_two_rows<NMAX, CPT, NCF, true>(ex, Ey + r * NMAX, Ey + (r + 1) * NMAX, NCF, a, b);
+      else
+        sums(r, TWO, a, b);
       if (!FAST && !col_ok) continue;
       if (MODE != kUnitMaxOnly) {
         const size_t o = off;
@@ -704,11 +705,26 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
       }
     }
   };
+  // FAST steps run the sums with a trip count fixed at compile time: the kept
+  // count rounded up to a quarter of NMAX (at least 4).  The table and column
+  // factors past the kept points are zeros, and a zero term leaves a sum of
+  // non-negative terms unchanged, so the padded sums have the same bits.
   const bool inside = x0 + kStrip <= ug.width;  // warp-uniform: every lane's columns
-  if (dsrc && mrow && grow && inside && (rows & 1) == 0)
-    rows_loop(std::true_type{});
-  else
-    rows_loop(std::false_type{});
+  using std::integral_constant;
+  constexpr int kQ = NMAX / 4 > 4 ? NMAX / 4 : 4;
+  if (dsrc && mrow && grow && inside && (rows & 1) == 0 && nc > 0) {
+    const int q = (nc + kQ - 1) / kQ;  // 1 .. NMAX / kQ
+    if (q >= NMAX / kQ)
+      rows_loop(std::true_type{}, integral_constant<int, NMAX>{});
+    else if (q == 1)
+      rows_loop(std::true_type{}, integral_constant<int, kQ>{});
+    else if (q == 2)
+      rows_loop(std::true_type{}, integral_constant<int, (2 * kQ < NMAX ? 2 * kQ : NMAX)>{});
+    else
+      rows_loop(std::true_type{}, integral_constant<int, (3 * kQ < NMAX ? 3 * kQ : NMAX)>{});
+  } else {
+    rows_loop(std::false_type{}, integral_constant<int, 0>{});
+  }
   cp_async_wait<0>();
   if (MODE != kUnitScaled) {
     unsigned long long key = 0ull;
