@@ -110,36 +110,48 @@ def _run_engine(mf, specs, chunk=7, graph=True, tune=True, only=None, offset=0, 
     return out, stats
 
 
-def test_engine_mixed_streams_match_oracle(mf):
-    outs, stats = _run_engine(mf, STREAMS)
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_engine_mixed_streams_match_oracle(mf, storage):
+    """Five streams on both map paths: with 16-bit maps the 130-pixel-wide
+    window-5 stream (not a multiple of the 16-point path's 4 columns per
+    lane) takes the 32-point path."""
+    dt = {"f32": torch.float32, "bf16": torch.bfloat16}[storage]
+    outs, stats = _run_engine(mf, STREAMS, dtype=dt)
     assert stats.ticks >= 6 and stats.frames == sum(s[6] for s in STREAMS)
     assert stats.graph_launches == stats.ticks
+    wide = 2 if storage == "f32" else 4
+    path16 = [s for s in STREAMS if s[2] <= 16 and s[0] % wide == 0]
+    assert stats.frames_path[1] == sum(s[6] for s in path16)
+    assert stats.frames_path[0] == stats.frames - stats.frames_path[1]
     for spec, (M, G, info) in zip(STREAMS, outs):
         width, height, window, smooth_len, mode, seed, frames = spec
         poses, depth, K = _inputs(spec)
         ref = O.OracleStream(O.Params(width, height, window=window, smooth_len=smooth_len,
                                       mode=O.MODE_ACCEL if mode == "accel" else O.MODE_HEADING))
-        ref.push(poses, depth.astype(np.float64), K)
+        ref.push(poses, torch.from_numpy(depth).to(dt).double().numpy(), K)
         intr = O.compensated_intrinsics(K, ref.p)
         for n in range(frames):
             rinfo, rp, Mr, Gr = ref.frame(n)
             parity.check_frame(info[n], None, rinfo, rp, intr, where=f"{spec} frame {n}",
                                size=(width, height))
-            parity.check_map(M[n], Mr, where=f"{spec} M {n}")
-            parity.check_map(G[n], Gr, where=f"{spec} G {n}")
-            parity.check_argmax(info[n], Mr, rinfo["n_valid"], where=f"{spec} argmax {n}")
+            parity.check_map(M[n], Mr, storage, where=f"{spec} M {n}")
+            parity.check_map(G[n], Gr, storage, where=f"{spec} G {n}")
+            parity.check_argmax(info[n], Mr, rinfo["n_valid"], storage, where=f"{spec} argmax {n}")
         assert info["n_valid"].sum() > 0
 
 
 @pytest.mark.parametrize("storage", ["f32", "bf16"])
 def test_engine_planes_aligned_to_two_elements(mf, storage):
-    """Planes shifted by two elements.  FP32 maps stay on the 16-point path
-    (2 pixels per lane: 8-byte accesses); 16-bit maps cannot take its
-    4-pixel accesses, and the engine renders those pushes on the 32-point
-    path.  Either way the maps match the oracle, with no fault or misread."""
+    """Planes shifted by two elements.  FP32 maps stay on their paths (2
+    pixels per lane: 8-byte accesses); 16-bit maps cannot take the 16-point
+    path's 4-pixel accesses, and the engine renders those pushes on the
+    32-point path.  Either way the maps match the oracle, with no fault or
+    misread."""
     dt = {"f32": torch.float32, "bf16": torch.bfloat16}[storage]
-    specs = [STREAMS[0], STREAMS[4]]      # both 16-point-path streams when aligned
-    outs, _ = _run_engine(mf, specs, offset=2, dtype=dt)
+    specs = [STREAMS[0], STREAMS[4], STREAMS[2]]   # two 16-point, one 32-point stream when aligned
+    outs, stats = _run_engine(mf, specs, offset=2, dtype=dt)
+    if storage == "bf16":
+        assert stats.frames_path[1] == 0 and stats.frames_path[0] == sum(s[6] for s in specs)
     ref_outs, _ = _run_engine(mf, specs, dtype=dt)
     for spec, (M, G, info), (Ma, Ga, infoa) in zip(specs, outs, ref_outs):
         width, height, window, smooth_len, mode, seed, frames = spec
