@@ -383,6 +383,13 @@ __device__ __forceinline__ void publish_key(FrameRec* rec, unsigned long long ke
   if ((threadIdx.x & 31) == 0 && any_points && key) atomicMax(&rec->argmax_key, key);
 }
 
+// Trip count of the fast row loop for q groups of 4 kept points (1 <= q):
+// 4 q, except that above 16 points counts up to 16 take 8 or 16 (fewer
+// compiled copies of the loop where they are rare).
+__host__ __device__ constexpr int padded_count(int nmax, int q) {
+  return 4 * q >= nmax ? nmax : (nmax > 16 && q <= 4 ? (q <= 2 ? 8 : 16) : 4 * q);
+}
+
 // One unit of one frame.  planes point at the frame's first pixel; the
 // caller guarantees width % CPT == 0 and CPT-element alignment of all
 // planes.  Every thread of the CTA must call this (it holds barriers).
@@ -706,24 +713,26 @@ __device__ __forceinline__ void map_unit(const UnitGeom& ug, float* Ey, uint4* m
     }
   };
   // FAST steps run the sums with a trip count fixed at compile time: the kept
-  // count rounded up to a quarter of NMAX (at least 4).  The table and column
-  // factors past the kept points are zeros, and a zero term leaves a sum of
-  // non-negative terms unchanged, so the padded sums have the same bits.
+  // count rounded up to a multiple of 4, and above 16 points of 8 when at
+  // most 16 are kept.  The table and column factors past the kept points
+  // are zeros, and a zero term leaves a sum of non-negative terms unchanged,
+  // so the padded sums have the same bits.
   const bool inside = x0 + kStrip <= ug.width;  // warp-uniform: every lane's columns
-  using std::integral_constant;
-  constexpr int kQ = NMAX / 4 > 4 ? NMAX / 4 : 4;
   if (dsrc && mrow && grow && inside && (rows & 1) == 0 && nc > 0) {
-    const int q = (nc + kQ - 1) / kQ;  // 1 .. NMAX / kQ
-    if (q >= NMAX / kQ)
-      rows_loop(std::true_type{}, integral_constant<int, NMAX>{});
-    else if (q == 1)
-      rows_loop(std::true_type{}, integral_constant<int, kQ>{});
-    else if (q == 2)
-      rows_loop(std::true_type{}, integral_constant<int, (2 * kQ < NMAX ? 2 * kQ : NMAX)>{});
-    else
-      rows_loop(std::true_type{}, integral_constant<int, (3 * kQ < NMAX ? 3 * kQ : NMAX)>{});
+    auto fast = [&](auto nc_tag) { rows_loop(std::true_type{}, nc_tag); };
+    using std::integral_constant;
+    switch (nc >> 2) {  // 1 .. NMAX / 4
+      case 1: fast(integral_constant<int, padded_count(NMAX, 1)>{}); break;
+      case 2: fast(integral_constant<int, padded_count(NMAX, 2)>{}); break;
+      case 3: fast(integral_constant<int, padded_count(NMAX, 3)>{}); break;
+      case 4: fast(integral_constant<int, padded_count(NMAX, 4)>{}); break;
+      case 5: fast(integral_constant<int, padded_count(NMAX, 5)>{}); break;
+      case 6: fast(integral_constant<int, padded_count(NMAX, 6)>{}); break;
+      case 7: fast(integral_constant<int, padded_count(NMAX, 7)>{}); break;
+      default: fast(integral_constant<int, NMAX>{}); break;
+    }
   } else {
-    rows_loop(std::false_type{}, integral_constant<int, 0>{});
+    rows_loop(std::false_type{}, std::integral_constant<int, 0>{});
   }
   cp_async_wait<0>();
   if (MODE != kUnitScaled) {
