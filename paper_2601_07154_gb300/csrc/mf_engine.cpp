@@ -416,7 +416,7 @@ int tune_class(mf_engine* e, int width, int height, int window, int* band_out) {
   ENG_CUDA(cudaStreamSynchronize(e->st), "stream sync before tuning");
   const size_t px = (size_t)width * height;
   const size_t per_frame = px * (dtype_bytes(e->d.depth_dtype) + 2 * dtype_bytes(e->d.map_dtype));
-  int frames = (int)std::max<size_t>(2, std::min<size_t>(64, ((size_t)1 << 30) / per_frame));
+  int frames = (int)std::max<size_t>(2, std::min<size_t>(64, ((size_t)4 << 30) / per_frame));
   frames = std::min(frames, e->d.max_tick_frames);
   char* buf = (char*)e->dalloc(per_frame * frames);
   if (!buf) return fail(MF_ERR_OOM, "tuning buffers");
@@ -463,9 +463,13 @@ int tune_class(mf_engine* e, int width, int height, int window, int* band_out) {
   pushes[0].slot = e->d.max_streams;
   std::vector<double> no_poses;
   const int path = stream_path(width, window, e->d.map_dtype);
-  for (int bh : band_candidates(height)) {
-    std::vector<TickFrame> frs(frames);
-    for (int f = 0; f < frames; ++f) {
+  // A candidate's cost is the time of all `frames` synthetic frames minus
+  // the time of the first half: the marginal time of a frame, without the
+  // launch's partly filled last wave of units (with few frames of one class
+  // that tail makes tall bands look slower than in a tick of many streams).
+  auto time_frames = [&](int bh, int nf, float* ms) -> int {
+    std::vector<TickFrame> frs(nf);
+    for (int f = 0; f < nf; ++f) {
       TickFrame& t = frs[f];
       std::memset(&t, 0, sizeof(t));
       t.push = 0;
@@ -490,9 +494,21 @@ int tune_class(mf_engine* e, int width, int height, int window, int* band_out) {
       ENG_CUDA(mf::launch_engine_map_only(args, e->d.depth_dtype, e->d.map_dtype, e->grids, e->st), "tune");
     ENG_CUDA(cudaEventRecord(b2, e->st), "event");
     ENG_CUDA(cudaEventSynchronize(b2), "event");
-    float ms = 0.0f;
-    ENG_CUDA(cudaEventElapsedTime(&ms, a, b2), "elapsed");
+    ENG_CUDA(cudaEventElapsedTime(ms, a, b2), "elapsed");
     e->launches += 4 * mf::kEnginePaths;
+    return MF_OK;
+  };
+  for (int bh : band_candidates(height)) {
+    float all = 0.0f, half = 0.0f;
+    int rc2 = time_frames(bh, frames, &all);
+    if (rc2 == MF_OK) rc2 = time_frames(bh, frames / 2, &half);
+    if (rc2 != MF_OK) {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b2);
+      e->dfree(buf, per_frame * frames);
+      return rc2;
+    }
+    const float ms = all - half;
     if (ms < best_ms) {
       best_ms = ms;
       best_band = bh;
